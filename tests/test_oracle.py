@@ -1,0 +1,330 @@
+"""Pins for the CPU oracle (no GPU).
+
+Each test checks the oracle against something other than itself: closed
+forms, invariants, special cases that reduce to textbook routines, an
+independent numpy brute force, and the exact-cover structure of the
+decompositions (Sec. 4, Theorem "Recursive Box-complement" and Corollary
+"Excluded-sum Components"; App. A for corners).
+"""
+
+import itertools
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2106_00124_gb300 import synth
+
+ALGOS_EX = ("brute", "box_complement")
+
+
+def _included(a, k, op, algo):
+    return {"brute": O.included_brute, "bdbs": O.bdbs}[algo](a, k, op)
+
+
+def _excluded(a, k, op, algo):
+    return {"brute": O.excluded_brute, "box_complement": O.box_complement,
+            "corners": O.corners}[algo](a, k, op)
+
+
+def _np_box_slices(x, k, shape):
+    return tuple(slice(xi, min(xi + ki, ni)) for xi, ki, ni in zip(x, k, shape))
+
+
+def _np_included(a, k, op):
+    """Independent numpy restatement of the definition (Sec. 2)."""
+    red = np.sum if op == "add" else np.max
+    out = np.empty(a.shape, dtype=np.float64 if a.dtype.kind == "f" else np.int64)
+    for x in itertools.product(*[range(n) for n in a.shape]):
+        out[x] = red(a[_np_box_slices(x, k, a.shape)].astype(out.dtype))
+    return out
+
+
+def _np_excluded(a, k, op):
+    """Independent numpy restatement of the definition (Sec. 2)."""
+    wide = a.astype(np.float64 if a.dtype.kind == "f" else np.int64)
+    out = np.empty(a.shape, dtype=wide.dtype)
+    for x in itertools.product(*[range(n) for n in a.shape]):
+        mask = np.ones(a.shape, dtype=bool)
+        mask[_np_box_slices(x, k, a.shape)] = False
+        vals = wide[mask]
+        if op == "add":
+            out[x] = vals.sum() if vals.size else 0
+        else:
+            out[x] = vals.max() if vals.size else O.identity("float" if a.dtype.kind == "f" else "int", "max")
+    return out
+
+
+SMALL_SHAPES = [(1,), (7,), (8,), (3, 5), (4, 4), (1, 6), (2, 3, 4), (3, 1, 5), (2, 2, 2, 3),
+                (2, 1, 2, 2, 2)]
+
+
+@pytest.mark.parametrize("shape", SMALL_SHAPES)
+@pytest.mark.parametrize("op", ["add", "max"])
+def test_brute_matches_numpy_definition(shape, op):
+    rng = np.random.default_rng(hash((shape, op)) & 0xFFFF)
+    a = rng.integers(-100, 100, size=shape).astype(np.int64)
+    for _ in range(3):
+        k = [int(rng.integers(1, n + 1)) for n in shape]
+        assert np.array_equal(O.included_brute(a, k, op), _np_included(a, k, op))
+        assert np.array_equal(O.excluded_brute(a, k, op), _np_excluded(a, k, op))
+
+
+def _all_k(shape):
+    return itertools.product(*[range(1, n + 1) for n in shape])
+
+
+EXHAUSTIVE_SHAPES = [(1,), (2,), (5,), (6,), (1, 1), (2, 3), (3, 3), (4, 2), (1, 4), (2, 2, 2),
+                     (3, 2, 4), (1, 3, 2), (2, 3, 2, 2), (2, 2, 1, 2, 2)]
+
+
+@pytest.mark.parametrize("shape", EXHAUSTIVE_SHAPES)
+@pytest.mark.parametrize("op", ["add", "max"])
+def test_algorithms_match_brute_every_k(shape, op):
+    """BDBS, box-complement and corners agree with the definition, bit for bit
+    on integers, for every box size k with 1 <= k_i <= n_i."""
+    rng = np.random.default_rng(len(shape) * 1000 + sum(shape))
+    a = rng.integers(-1000, 1000, size=shape).astype(np.int64)
+    for k in _all_k(shape):
+        inc = O.included_brute(a, k, op)
+        exc = O.excluded_brute(a, k, op)
+        assert np.array_equal(O.bdbs(a, k, op), inc), k
+        assert np.array_equal(O.box_complement(a, k, op), exc), k
+        if len(shape) in (2, 3):
+            assert np.array_equal(O.corners(a, k, op), exc), k
+        if op == "add":
+            assert np.array_equal(O.sat_included(a, k), inc), k
+            assert np.array_equal(O.bdbsc(a, k), exc), k
+
+
+@pytest.mark.parametrize("shape", [(9,), (5, 7), (4, 5, 6), (3, 4, 3, 4)])
+@pytest.mark.parametrize("op", ["add", "max"])
+def test_float_algorithms_match_brute(shape, op):
+    """float64: max is exact; + agrees to rounding (operands reassociate)."""
+    a = synth.uniform_f32(shape, seed=sum(shape)).astype(np.float64)
+    rng = np.random.default_rng(7)
+    for _ in range(4):
+        k = [int(rng.integers(1, n + 1)) for n in shape]
+        inc, exc = O.included_brute(a, k, op), O.excluded_brute(a, k, op)
+        got_inc, got_exc = O.bdbs(a, k, op), O.box_complement(a, k, op)
+        if op == "max":
+            assert np.array_equal(got_inc, inc) and np.array_equal(got_exc, exc)
+        else:
+            scale = max(1.0, float(np.abs(exc).max()))
+            assert np.max(np.abs(got_inc - inc)) <= 1e-12 * scale
+            assert np.max(np.abs(got_exc - exc)) <= 1e-12 * scale
+
+
+@pytest.mark.parametrize("shape", [(6,), (4, 7), (3, 5, 4), (2, 3, 2, 3)])
+def test_closed_form_ones(shape):
+    """A = 1 with +: included[x] = prod_i min(k_i, n_i - x_i), excluded = N - that."""
+    a = np.ones(shape, dtype=np.int64)
+    N = a.size
+    rng = np.random.default_rng(11)
+    for _ in range(5):
+        k = [int(rng.integers(1, n + 1)) for n in shape]
+        grids = np.meshgrid(*[np.arange(n) for n in shape], indexing="ij")
+        expect = np.ones(shape, dtype=np.int64)
+        for g, ki, ni in zip(grids, k, shape):
+            expect = expect * np.minimum(ki, ni - g)
+        assert np.array_equal(O.included_brute(a, k, "add"), expect)
+        assert np.array_equal(O.bdbs(a, k, "add"), expect)
+        assert np.array_equal(O.excluded_brute(a, k, "add"), N - expect)
+        assert np.array_equal(O.box_complement(a, k, "add"), N - expect)
+        if len(shape) in (2, 3):
+            assert np.array_equal(O.corners(a, k, "add"), N - expect)
+
+
+@pytest.mark.parametrize("shape", [(7,), (4, 6), (3, 4, 5), (2, 3, 3, 2)])
+def test_closed_form_linear_index_max(shape):
+    """A[y] = row-major index of y with max: the included max sits at the box's
+    far corner min(x + k, n) - 1; the excluded max is N - 1 whenever the box
+    misses the tensor's last element, and e when the box is the whole tensor."""
+    N = int(np.prod(shape))
+    a = np.arange(N, dtype=np.int64).reshape(shape)
+    rng = np.random.default_rng(5)
+    for _ in range(6):
+        k = [int(rng.integers(1, n + 1)) for n in shape]
+        grids = np.meshgrid(*[np.arange(n) for n in shape], indexing="ij")
+        far = [np.minimum(g + ki, ni) - 1 for g, ki, ni in zip(grids, k, shape)]
+        expect_inc = np.ravel_multi_index(far, shape)
+        assert np.array_equal(O.included_brute(a, k, "max"), expect_inc)
+        assert np.array_equal(O.bdbs(a, k, "max"), expect_inc)
+        exc = O.excluded_brute(a, k, "max")
+        bc = O.box_complement(a, k, "max")
+        assert np.array_equal(exc, bc)
+        covers_last = np.ones(shape, dtype=bool)
+        for g, ki, ni in zip(grids, k, shape):
+            covers_last &= (g + ki >= ni)
+        assert np.all(exc[~covers_last] == N - 1)
+    full = list(shape)
+    e = O.identity("int", "max")
+    assert O.excluded_brute(a, full, "max").flat[0] == e
+    assert O.box_complement(a, full, "max").flat[0] == e
+
+
+@pytest.mark.parametrize("shape", [(10,), (6, 5), (4, 3, 5), (3, 2, 3, 2)])
+def test_invariant_add_total(shape):
+    """For +: included + excluded = total, exactly in int64 (Sec. 1, weak form)."""
+    a = synth.uniform_int(shape, -1000, 1000, seed=3)
+    total = int(a.sum())
+    rng = np.random.default_rng(1)
+    for _ in range(5):
+        k = [int(rng.integers(1, n + 1)) for n in shape]
+        assert np.all(O.bdbs(a, k, "add") + O.box_complement(a, k, "add") == total)
+
+
+@pytest.mark.parametrize("shape", [(10,), (6, 5), (4, 3, 5)])
+def test_invariant_max_global(shape):
+    """For max: max(included, excluded) = the global maximum."""
+    a = synth.uniform_int(shape, -1000, 1000, seed=4)
+    rng = np.random.default_rng(2)
+    for _ in range(5):
+        k = [int(rng.integers(1, n + 1)) for n in shape]
+        both = np.maximum(O.bdbs(a, k, "max"), O.box_complement(a, k, "max"))
+        assert np.all(both == a.max())
+
+
+@pytest.mark.parametrize("shape", [(9,), (5, 4), (3, 4, 2)])
+@pytest.mark.parametrize("op", ["add", "max"])
+def test_k_one_and_k_full(shape, op):
+    """k = 1: included = A.  k = n: included[0] = total, excluded[0] = e."""
+    a = synth.uniform_int(shape, -50, 50, seed=5)
+    ones = [1] * len(shape)
+    assert np.array_equal(O.bdbs(a, ones, op), a)
+    full = list(shape)
+    red = a.sum() if op == "add" else a.max()
+    assert O.bdbs(a, full, op).flat[0] == red
+    assert O.box_complement(a, full, op).flat[0] == O.identity("int", op)
+
+
+@pytest.mark.parametrize("n,k", [(1, 1), (8, 4), (13, 5), (16, 16), (31, 1), (64, 7)])
+@pytest.mark.parametrize("op", ["add", "max"])
+def test_d1_prefix_suffix_formula(n, k, op):
+    """d = 1: excluded[x] = exclusive prefix at x (+) suffix from x + k, each a
+    textbook scan (numpy cumsum / maximum.accumulate)."""
+    a = synth.uniform_int((n,), -1000, 1000, seed=n * 31 + k)
+    e = O.identity("int", op)
+    if op == "add":
+        pre = np.concatenate([[0], np.cumsum(a)[:-1]])
+        suf = np.concatenate([np.cumsum(a[::-1])[::-1], [0]])
+        expect = pre + suf[np.minimum(np.arange(n) + k, n)]
+    else:
+        pre = np.concatenate([[e], np.maximum.accumulate(a)[:-1]])
+        suf = np.concatenate([np.maximum.accumulate(a[::-1])[::-1], [e]])
+        expect = np.maximum(pre, suf[np.minimum(np.arange(n) + k, n)])
+    assert np.array_equal(O.box_complement(a, [k], op), expect)
+    assert np.array_equal(O.excluded_brute(a, [k], op), expect)
+
+
+@pytest.mark.parametrize("shape", [(9, 7), (16, 5)])
+def test_d2_inclusion_exclusion(shape):
+    """d = 2, +: included sums from a numpy summed-area table by inclusion-exclusion."""
+    a = synth.uniform_int(shape, -1000, 1000, seed=6)
+    sat = np.zeros((shape[0] + 1, shape[1] + 1), dtype=np.int64)
+    sat[1:, 1:] = a.cumsum(0).cumsum(1)
+    rng = np.random.default_rng(3)
+    for _ in range(5):
+        k1, k2 = [int(rng.integers(1, n + 1)) for n in shape]
+        i = np.arange(shape[0])[:, None]
+        j = np.arange(shape[1])[None, :]
+        i2, j2 = np.minimum(i + k1, shape[0]), np.minimum(j + k2, shape[1])
+        expect = sat[i2, j2] - sat[i, j2] - sat[i2, j] + sat[i, j]
+        assert np.array_equal(O.bdbs(a, [k1, k2], "add"), expect)
+
+
+def test_int32_wraps_like_int32():
+    """int32 + wraps modulo 2^32: the low 32 bits of the oracle's int64 result
+    equal a wrapping int32 reduction done by numpy."""
+    shape = (6, 7)
+    a = synth.uniform_int(shape, -(1 << 31), (1 << 31) - 1, seed=8, dtype=np.int32)
+    k = (3, 4)
+    got = O.bdbs(a, k, "add").astype(np.int32)
+    expect = np.empty(shape, dtype=np.int32)
+    with np.errstate(over="ignore"):
+        for x in itertools.product(range(6), range(7)):
+            expect[x] = a[_np_box_slices(x, k, shape)].sum(dtype=np.int32)
+    assert np.array_equal(got, expect)
+    exc = O.box_complement(a, k, "add").astype(np.int32)
+    with np.errstate(over="ignore"):
+        total = a.sum(dtype=np.int32)
+        assert np.array_equal((exc + got).astype(np.int32), np.full(shape, total, dtype=np.int32))
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_corner_regions_partition_complement(d):
+    """The corners regions (App. A) cover the 3^d - 1 cells outside the box
+    exactly once and never the box itself.  Per dimension the cells are
+    below (y < x), inside (x <= y < x+k) and above (y >= x+k)."""
+    count = {cell: 0 for cell in itertools.product(range(3), repeat=d)}
+    for mask in range(1 << d):
+        allowed = []
+        for dim in range(d):
+            suffix = (mask >> dim) & 1
+            hi = O.corner_threshold_hi(d, dim, mask)
+            if not suffix:
+                allowed.append({0, 1} if hi else {0})
+            else:
+                allowed.append({2} if hi else {1, 2})
+        for cell in itertools.product(*allowed):
+            count[cell] += 1
+    inside = (1,) * d
+    assert count[inside] == 0
+    assert all(c == 1 for cell, c in count.items() if cell != inside)
+
+
+@pytest.mark.parametrize("shape", [(4, 3), (3, 4, 3), (2, 3, 2, 3)])
+def test_box_complement_components_partition(shape):
+    """Corollary (Excluded-sum Components): the 2d regions
+    (:, .., :, :x_i, x_{i+1}:x'_{i+1}, ..) and (:, .., :, x_i+k_i:, x_{i+1}:x'_{i+1}, ..)
+    for i = 1..d are disjoint and their union is the complement of the box."""
+    d = len(shape)
+    k = [max(1, n // 2) for n in shape]
+    for x in itertools.product(*[range(n) for n in shape]):
+        for y in itertools.product(*[range(n) for n in shape]):
+            hits = 0
+            for i in range(d):
+                tail = all(x[m] <= y[m] < x[m] + k[m] for m in range(i + 1, d))
+                if tail and y[i] < x[i]:
+                    hits += 1
+                if tail and y[i] >= x[i] + k[i]:
+                    hits += 1
+            in_box = all(x[m] <= y[m] < x[m] + k[m] for m in range(d))
+            assert hits == (0 if in_box else 1)
+
+
+def test_operation_counts_3d():
+    """Sec. 6 ("Excluded Sums With Different Operators"): in 3D box-complement
+    performs about 12 operator applications per element and the best corners
+    variant about 22, a ratio near 1.8.  The counting convention is not
+    stated; this oracle counts every application including the additions
+    into the output, and its corners variant recomputes each leaf, so only
+    the ratio is pinned, loosely."""
+    a = np.ones((24, 24, 24), dtype=np.int64)
+    O.reset_ops()
+    O.box_complement(a, [4, 4, 4], "add")
+    bc = O.get_ops() / a.size
+    O.reset_ops()
+    O.corners(a, [4, 4, 4], "add")
+    cn = O.get_ops() / a.size
+    assert 10 <= bc <= 20
+    assert 1.5 <= cn / bc <= 2.2
+
+
+def test_point_queries_match_full():
+    a = synth.uniform_int((5, 6, 4), -100, 100, seed=9)
+    k = (2, 3, 2)
+    inc, exc = O.included_brute(a, k, "add"), O.excluded_brute(a, k, "max")
+    for x in [(0, 0, 0), (4, 5, 3), (2, 4, 1), (3, 0, 2)]:
+        assert O.included_at(a, k, "add", x) == inc[x]
+        assert O.excluded_at(a, k, "max", x) == exc[x]
+
+
+def test_invalid_arguments_rejected():
+    a = np.zeros((4, 4), dtype=np.int64)
+    with pytest.raises(ValueError):
+        O.bdbs(a, [0, 1], "add")
+    with pytest.raises(ValueError):
+        O.box_complement(a, [5, 1], "add")
+    with pytest.raises(ValueError):
+        O.corners(np.zeros((4,), dtype=np.int64), [1], "add")
