@@ -1,0 +1,139 @@
+/*
+ * exsum.h -- C ABI of a GB300 (sm_103a) CUDA library for multidimensional
+ * included and excluded sums (Xu, Fraser, Leiserson, "Multidimensional
+ * Included and Excluded Sums", SIAM ACDA 2021).
+ *
+ * Problem (Sec. 2, Definition "Included and Excluded Sums"): for a
+ * d-dimensional tensor A of shape n_1 x ... x n_d, a box size
+ * k = (k_1, ..., k_d) and an associative, commutative operator (+) with
+ * identity e, the INCLUDED sum at x reduces A over the box
+ * [x_1, x_1+k_1) x ... x [x_d, x_d+k_d) clipped to the tensor (Sec. 2,
+ * colon notation), and the EXCLUDED sum at x reduces A over every coordinate
+ * outside that box (the "strong" problem of Sec. 1: no inverse is used).
+ *
+ * Common conventions for every entry point below
+ *   Layout      Tensors are dense and row-major: dimension d (index d-1 in
+ *               `shape`) is contiguous, dimension 1 is the slowest.
+ *   Pointers    `in` and `out` are DEVICE pointers on the current CUDA
+ *               device.  `in` is read only; `out` must not overlap `in`.
+ *               The caller owns both.  `shape` and `k` are HOST arrays of
+ *               `d` entries, read during the call only.
+ *   Types       in dtype -> out dtype:  I32 -> I32, I64 -> I64,
+ *               F32 -> F32, BF16 -> F32 (bf16 inputs are accumulated and
+ *               returned in fp32).  Integer + wraps modulo 2^32 / 2^64, so
+ *               integer results are exact and order-independent; max is
+ *               exact.  Floating-point + accumulates in fp32 with
+ *               compensated (two-sum) carries on every long reduction.
+ *   Arguments   1 <= d <= EXSUM_MAX_DIMS, n_i >= 1, 1 <= k_i <= n_i
+ *               (Sec. 1 requires k_i <= n_i); anything else returns
+ *               EXSUM_EINVAL before any work is queued.
+ *   Streams     `stream` is a cudaStream_t (NULL = legacy default stream).
+ *               Work is queued asynchronously on it; nothing synchronises
+ *               unless stated.  Results are ready when the stream reaches
+ *               the point after the call.
+ *   Errors      0 on success, a negative EXSUM_E* code otherwise.  A CUDA
+ *               error is reported as EXSUM_ECUDA; exsum_last_cuda_error()
+ *               returns the underlying cudaError_t of the calling thread.
+ *               On error, the contents of `out` are unspecified.
+ */
+#ifndef EXSUM_H
+#define EXSUM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define EXSUM_MAX_DIMS 8
+
+typedef enum { EXSUM_OP_ADD = 0, EXSUM_OP_MAX = 1 } exsum_op;
+
+typedef enum { EXSUM_I32 = 0, EXSUM_I64 = 1, EXSUM_F32 = 2, EXSUM_BF16 = 3 } exsum_dtype;
+
+enum {
+    EXSUM_OK = 0,
+    EXSUM_EINVAL = -1,      /* invalid argument (shape, box, dtype, op, pointer) */
+    EXSUM_ENOMEM = -2,      /* workspace too small, or an allocation failed */
+    EXSUM_EUNSUPPORTED = -3,/* valid request this build does not handle */
+    EXSUM_ECUDA = -4,       /* a CUDA runtime call failed; see exsum_last_cuda_error */
+    EXSUM_ETIMEDOUT = -5,   /* a bounded host-side wait ran out */
+    EXSUM_EBUSY = -6        /* resource busy (server full, capture in progress) */
+};
+
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+int exsum_version(void);
+
+/* Static description of a status code (never NULL). */
+const char *exsum_strerror(int status);
+
+/* The cudaError_t (as int) behind the calling thread's last EXSUM_ECUDA. */
+int exsum_last_cuda_error(void);
+
+/* Output dtype for an input dtype (BF16 -> F32, others unchanged); -1 if
+ * `dtype` is not an exsum_dtype. */
+int exsum_out_dtype(int dtype);
+
+/* Bytes per element of a dtype; 0 if unknown. */
+size_t exsum_dtype_size(int dtype);
+
+/*
+ * Workspace needed by exsum_included_ws (excluded == 0) or
+ * exsum_excluded_ws (excluded != 0) for this problem, in bytes.  Returns 0
+ * with *status = EXSUM_EINVAL for invalid arguments (status may be NULL).
+ * The figure includes 256-byte alignment padding of each sub-buffer.
+ */
+size_t exsum_workspace_bytes(int d, const int64_t *shape, const int64_t *k, int op, int dtype,
+                             int excluded, int *status);
+
+/*
+ * Included sums by BDBS (Sec. 3, "Included Sums in 1D" and "Generalizing to
+ * Arbitrary Dimensions"): the k-blocked Range-Prefix-Row / Range-Suffix-Row
+ * scans and Combine-Along-Row of BDBS-1D applied along dimensions d, ..., 1
+ * in turn (BDBS-Along-Dim, Sec. 5).  out[x] = (+) over the clipped box at x.
+ * `out` has the output dtype and the same shape.  Uses a workspace that the
+ * library allocates and caches per device (cudaMalloc on first use or
+ * growth, outside any stream capture; a call made while `stream` is being
+ * captured that would need to grow the cache returns EXSUM_EBUSY).
+ */
+int exsum_included(const void *in, void *out, int d, const int64_t *shape, const int64_t *k,
+                   int op, int dtype, void *stream);
+
+/* As exsum_included, with a caller-owned DEVICE workspace of at least
+ * exsum_workspace_bytes(..., excluded = 0) bytes (EXSUM_ENOMEM if smaller).
+ * Allocates nothing; safe to capture in a CUDA graph. */
+int exsum_included_ws(const void *in, void *out, int d, const int64_t *shape, const int64_t *k,
+                      int op, int dtype, void *workspace, size_t workspace_bytes, void *stream);
+
+/*
+ * Excluded sums by the box-complement algorithm (Sec. 4, Theorem "Recursive
+ * Box-complement" and Corollary "Excluded-sum Components"; Sec. 5,
+ * Fig. "exsum-code").  For each x the complement of the box is split into
+ * the 2d disjoint regions of the Corollary; region pair i is the prefix and
+ * the suffix along dimension i of the tensor reduced over dimensions < i
+ * (Prefix-Along-Dim / Suffix-Along-Dim) with included sums along the
+ * dimensions > i (BDBS-Along-Dim), added in by Add-Contribution.
+ * The GPU schedule applies the included sums along dimensions > i before the
+ * prefix/suffix along dimension i (both reduce over product sets, so the
+ * order is immaterial for a commutative operator), which needs one BDBS per
+ * step instead of two; see the library's design notes.
+ * Same arguments, ownership and workspace policy as exsum_included.
+ */
+int exsum_excluded(const void *in, void *out, int d, const int64_t *shape, const int64_t *k,
+                   int op, int dtype, void *stream);
+
+/* As exsum_excluded, with a caller-owned DEVICE workspace of at least
+ * exsum_workspace_bytes(..., excluded = 1) bytes.  Allocates nothing. */
+int exsum_excluded_ws(const void *in, void *out, int d, const int64_t *shape, const int64_t *k,
+                      int op, int dtype, void *workspace, size_t workspace_bytes, void *stream);
+
+/* Frees the library's cached per-device workspaces (synchronises the
+ * device first).  Returns 0 or EXSUM_ECUDA. */
+int exsum_release_cached_workspace(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EXSUM_H */

@@ -1,1 +1,189 @@
-"""GB300 (sm_103a) CUDA library for multidimensional included and excluded sums."""
+"""GB300 (sm_103a) CUDA library for multidimensional included and excluded sums.
+
+Xu, Fraser, Leiserson, "Multidimensional Included and Excluded Sums"
+(SIAM ACDA 2021): BDBS for included sums (Sec. 3) and box-complement for
+strong excluded sums (Sec. 4-5), as hand-written CUDA behind a small C ABI
+(``include/exsum.h``).
+
+This module is a thin ctypes binding: the functions named ``exsum_*`` take
+the same arguments as the C entry points (device pointers as integers, host
+sequences for shape and box, a cudaStream_t as an integer) and return the C
+status code.  ``included`` / ``excluded`` are conveniences over torch CUDA
+tensors that allocate the output and raise ``ExsumError`` on failure.  All
+arithmetic runs in the CUDA library; there is no CPU fallback, and calling
+anything without the built library raises.
+"""
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libexsum.so")
+
+OP_ADD, OP_MAX = 0, 1
+I32, I64, F32, BF16 = 0, 1, 2, 3
+EXSUM_OK, EXSUM_EINVAL, EXSUM_ENOMEM, EXSUM_EUNSUPPORTED, EXSUM_ECUDA, EXSUM_ETIMEDOUT, EXSUM_EBUSY = (
+    0, -1, -2, -3, -4, -5, -6)
+MAX_DIMS = 8
+
+OPS = {"add": OP_ADD, "max": OP_MAX}
+DTYPES = {"i32": I32, "i64": I64, "f32": F32, "bf16": BF16}
+
+
+class ExsumError(RuntimeError):
+    """A non-zero status from the C library."""
+
+    def __init__(self, status, what=""):
+        self.status = status
+        msg = "%s: %s (status %d)" % (what or "exsum", strerror(status), status)
+        if status == EXSUM_ECUDA:
+            msg += ", cudaError %d" % _load().exsum_last_cuda_error()
+        super().__init__(msg)
+
+
+_lib = None
+
+_P = ctypes.c_void_p
+_I64P = ctypes.POINTER(ctypes.c_int64)
+_SIG = {
+    "exsum_version": ([], ctypes.c_int),
+    "exsum_strerror": ([ctypes.c_int], ctypes.c_char_p),
+    "exsum_last_cuda_error": ([], ctypes.c_int),
+    "exsum_out_dtype": ([ctypes.c_int], ctypes.c_int),
+    "exsum_dtype_size": ([ctypes.c_int], ctypes.c_size_t),
+    "exsum_workspace_bytes": ([ctypes.c_int, _I64P, _I64P, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                               ctypes.POINTER(ctypes.c_int)], ctypes.c_size_t),
+    "exsum_included": ([_P, _P, ctypes.c_int, _I64P, _I64P, ctypes.c_int, ctypes.c_int, _P],
+                       ctypes.c_int),
+    "exsum_excluded": ([_P, _P, ctypes.c_int, _I64P, _I64P, ctypes.c_int, ctypes.c_int, _P],
+                       ctypes.c_int),
+    "exsum_included_ws": ([_P, _P, ctypes.c_int, _I64P, _I64P, ctypes.c_int, ctypes.c_int, _P,
+                           ctypes.c_size_t, _P], ctypes.c_int),
+    "exsum_excluded_ws": ([_P, _P, ctypes.c_int, _I64P, _I64P, ctypes.c_int, ctypes.c_int, _P,
+                           ctypes.c_size_t, _P], ctypes.c_int),
+    "exsum_release_cached_workspace": ([], ctypes.c_int),
+}
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                "the CUDA library %s is not built; run `python -m paper_2106_00124_gb300.build` "
+                "(or __graft_entry__.build()) on a machine with nvcc" % LIB_PATH)
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, (args, res) in _SIG.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+    return _lib
+
+
+def declared_symbols():
+    """Names of the C entry points this binding expects the library to export."""
+    return sorted(_SIG)
+
+
+def _arr(seq):
+    return (ctypes.c_int64 * len(seq))(*[int(v) for v in seq])
+
+
+# ---- C-ABI mirrors: argument marshalling only -------------------------------------------------
+
+def exsum_version():
+    return _load().exsum_version()
+
+
+def strerror(status):
+    return _load().exsum_strerror(int(status)).decode()
+
+
+exsum_strerror = strerror
+
+
+def exsum_last_cuda_error():
+    return _load().exsum_last_cuda_error()
+
+
+def exsum_out_dtype(dtype):
+    return _load().exsum_out_dtype(int(dtype))
+
+
+def exsum_dtype_size(dtype):
+    return _load().exsum_dtype_size(int(dtype))
+
+
+def exsum_workspace_bytes(d, shape, k, op, dtype, excluded):
+    """Returns (bytes, status)."""
+    st = ctypes.c_int(0)
+    b = _load().exsum_workspace_bytes(int(d), _arr(shape), _arr(k), int(op), int(dtype),
+                                      int(bool(excluded)), ctypes.byref(st))
+    return int(b), st.value
+
+
+def exsum_included(in_ptr, out_ptr, d, shape, k, op, dtype, stream=0):
+    return _load().exsum_included(in_ptr, out_ptr, int(d), _arr(shape), _arr(k), int(op),
+                                  int(dtype), stream or None)
+
+
+def exsum_excluded(in_ptr, out_ptr, d, shape, k, op, dtype, stream=0):
+    return _load().exsum_excluded(in_ptr, out_ptr, int(d), _arr(shape), _arr(k), int(op),
+                                  int(dtype), stream or None)
+
+
+def exsum_included_ws(in_ptr, out_ptr, d, shape, k, op, dtype, ws_ptr, ws_bytes, stream=0):
+    return _load().exsum_included_ws(in_ptr, out_ptr, int(d), _arr(shape), _arr(k), int(op),
+                                     int(dtype), ws_ptr, int(ws_bytes), stream or None)
+
+
+def exsum_excluded_ws(in_ptr, out_ptr, d, shape, k, op, dtype, ws_ptr, ws_bytes, stream=0):
+    return _load().exsum_excluded_ws(in_ptr, out_ptr, int(d), _arr(shape), _arr(k), int(op),
+                                     int(dtype), ws_ptr, int(ws_bytes), stream or None)
+
+
+def exsum_release_cached_workspace():
+    return _load().exsum_release_cached_workspace()
+
+
+# ---- torch conveniences ------------------------------------------------------------------------
+
+def torch_dtype_code(t):
+    """exsum dtype code of a torch tensor (int32, int64, float32, bfloat16)."""
+    import torch
+    table = {torch.int32: I32, torch.int64: I64, torch.float32: F32, torch.bfloat16: BF16}
+    if t.dtype not in table:
+        raise ExsumError(EXSUM_EINVAL, "unsupported tensor dtype %s" % t.dtype)
+    return table[t.dtype]
+
+
+def _out_like(x, dtype):
+    import torch
+    out_dtype = {I32: torch.int32, I64: torch.int64, F32: torch.float32, BF16: torch.float32}[dtype]
+    return torch.empty(x.shape, dtype=out_dtype, device=x.device)
+
+
+def _torch_call(fn, x, k, op, out, what):
+    import torch
+    if not x.is_cuda or not x.is_contiguous():
+        raise ExsumError(EXSUM_EINVAL, what + ": input must be a contiguous CUDA tensor")
+    dt = torch_dtype_code(x)
+    if out is None:
+        out = _out_like(x, dt)
+    stream = torch.cuda.current_stream(x.device).cuda_stream
+    with torch.cuda.device(x.device):
+        rc = fn(x.data_ptr(), out.data_ptr(), x.dim(), list(x.shape), list(k), OPS[op], dt, stream)
+    if rc != EXSUM_OK:
+        raise ExsumError(rc, what)
+    return out
+
+
+def included(x, k, op="add", out=None):
+    """Included sums of a contiguous CUDA tensor (bf16 -> fp32 output)."""
+    return _torch_call(exsum_included, x, k, op, out, "exsum_included")
+
+
+def excluded(x, k, op="add", out=None):
+    """Strong excluded sums of a contiguous CUDA tensor (bf16 -> fp32 output)."""
+    return _torch_call(exsum_excluded, x, k, op, out, "exsum_excluded")

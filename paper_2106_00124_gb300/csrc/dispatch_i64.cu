@@ -1,0 +1,17 @@
+// Instantiates the included/excluded pipelines for I64 inputs (both operators).
+#include "pipeline.cuh"
+
+namespace exsum {
+
+int dispatch_i64(int op, int excluded, const void *in, void *out, int d, const int64_t *n,
+                   const int64_t *k, void *ws, size_t ws_bytes, cudaStream_t stream,
+                   size_t *ws_needed, cudaError_t *cuda_err)
+{
+    if (op == OP_ADD)
+        return Pipe<M_I64_ADD>::run(excluded, in, out, d, n, k, ws, ws_bytes, stream, ws_needed,
+                                     cuda_err);
+    return Pipe<M_I64_MAX>::run(excluded, in, out, d, n, k, ws, ws_bytes, stream, ws_needed,
+                                 cuda_err);
+}
+
+}  // namespace exsum

@@ -1,0 +1,228 @@
+// exsum_abi.cu -- the C ABI declared in include/exsum.h: argument checks,
+// dtype/operator dispatch, and the per-(device, stream) workspace cache.
+#include <cuda_runtime.h>
+
+#include <map>
+#include <mutex>
+#include <utility>
+
+#include "../../include/exsum.h"
+#include "pipeline.cuh"
+
+namespace exsum {
+int dispatch_i32(int, int, const void *, void *, int, const int64_t *, const int64_t *, void *,
+                 size_t, cudaStream_t, size_t *, cudaError_t *);
+int dispatch_i64(int, int, const void *, void *, int, const int64_t *, const int64_t *, void *,
+                 size_t, cudaStream_t, size_t *, cudaError_t *);
+int dispatch_f32(int, int, const void *, void *, int, const int64_t *, const int64_t *, void *,
+                 size_t, cudaStream_t, size_t *, cudaError_t *);
+int dispatch_bf16(int, int, const void *, void *, int, const int64_t *, const int64_t *, void *,
+                  size_t, cudaStream_t, size_t *, cudaError_t *);
+}  // namespace exsum
+
+static thread_local int g_last_cuda_error = 0;
+
+static int validate(int d, const int64_t *shape, const int64_t *k, int op, int dtype)
+{
+    if (d < 1 || d > EXSUM_MAX_DIMS || !shape || !k) return EXSUM_EINVAL;
+    if (op != EXSUM_OP_ADD && op != EXSUM_OP_MAX) return EXSUM_EINVAL;
+    if (dtype < EXSUM_I32 || dtype > EXSUM_BF16) return EXSUM_EINVAL;
+    int64_t N = 1;
+    for (int i = 0; i < d; ++i) {
+        if (shape[i] < 1 || k[i] < 1 || k[i] > shape[i]) return EXSUM_EINVAL;
+        if (N > ((int64_t)1 << 62) / shape[i]) return EXSUM_EINVAL;  // element count overflow
+        N *= shape[i];
+    }
+    return EXSUM_OK;
+}
+
+static int run(int excluded, const void *in, void *out, int d, const int64_t *shape,
+               const int64_t *k, int op, int dtype, void *ws, size_t ws_bytes, void *stream,
+               size_t *need)
+{
+    cudaError_t ce = cudaSuccess;
+    int rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    switch (dtype) {
+    case EXSUM_I32: rc = exsum::dispatch_i32(op, excluded, in, out, d, shape, k, ws, ws_bytes, st, need, &ce); break;
+    case EXSUM_I64: rc = exsum::dispatch_i64(op, excluded, in, out, d, shape, k, ws, ws_bytes, st, need, &ce); break;
+    case EXSUM_F32: rc = exsum::dispatch_f32(op, excluded, in, out, d, shape, k, ws, ws_bytes, st, need, &ce); break;
+    default: rc = exsum::dispatch_bf16(op, excluded, in, out, d, shape, k, ws, ws_bytes, st, need, &ce); break;
+    }
+    if (rc == EXSUM_ECUDA) g_last_cuda_error = (int)ce;
+    return rc;
+}
+
+// ---- workspace cache: one growing buffer per (device, stream) --------------------------------
+namespace {
+struct CacheEntry {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+};
+std::mutex g_cache_mu;
+std::map<std::pair<int, void *>, CacheEntry> g_cache;
+}  // namespace
+
+static int cached_workspace(void *stream, size_t need, void **ws, size_t *ws_bytes)
+{
+    *ws = nullptr;
+    *ws_bytes = 0;
+    if (need == 0) return EXSUM_OK;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        g_last_cuda_error = (int)e;
+        return EXSUM_ECUDA;
+    }
+    std::lock_guard<std::mutex> lock(g_cache_mu);
+    CacheEntry &ent = g_cache[std::make_pair(dev, stream)];
+    if (ent.bytes < need) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        e = cudaStreamIsCapturing((cudaStream_t)stream, &cs);
+        if (e != cudaSuccess) {
+            g_last_cuda_error = (int)e;
+            return EXSUM_ECUDA;
+        }
+        if (cs != cudaStreamCaptureStatusNone) return EXSUM_EBUSY;
+        if (ent.ptr) {
+            // Earlier work on this stream may still use the old buffer.
+            e = cudaStreamSynchronize((cudaStream_t)stream);
+            if (e == cudaSuccess) e = cudaFree(ent.ptr);
+            ent.ptr = nullptr;
+            ent.bytes = 0;
+            if (e != cudaSuccess) {
+                g_last_cuda_error = (int)e;
+                return EXSUM_ECUDA;
+            }
+        }
+        const size_t grow = need + need / 4;
+        e = cudaMalloc(&ent.ptr, grow);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            ent.ptr = nullptr;
+            g_last_cuda_error = (int)e;
+            return EXSUM_ENOMEM;
+        }
+        ent.bytes = grow;
+    }
+    *ws = ent.ptr;
+    *ws_bytes = ent.bytes;
+    return EXSUM_OK;
+}
+
+static int call_cached(int excluded, const void *in, void *out, int d, const int64_t *shape,
+                       const int64_t *k, int op, int dtype, void *stream)
+{
+    int rc = validate(d, shape, k, op, dtype);
+    if (rc) return rc;
+    if (!in || !out) return EXSUM_EINVAL;
+    size_t need = 0;
+    rc = run(excluded, nullptr, nullptr, d, shape, k, op, dtype, nullptr, 0, nullptr, &need);
+    if (rc) return rc;
+    void *ws = nullptr;
+    size_t wsb = 0;
+    rc = cached_workspace(stream, need, &ws, &wsb);
+    if (rc) return rc;
+    return run(excluded, in, out, d, shape, k, op, dtype, ws, wsb, stream, nullptr);
+}
+
+extern "C" {
+
+int exsum_version(void) { return 10000; }
+
+const char *exsum_strerror(int status)
+{
+    switch (status) {
+    case EXSUM_OK: return "success";
+    case EXSUM_EINVAL: return "invalid argument";
+    case EXSUM_ENOMEM: return "workspace too small or allocation failed";
+    case EXSUM_EUNSUPPORTED: return "unsupported request";
+    case EXSUM_ECUDA: return "CUDA runtime error";
+    case EXSUM_ETIMEDOUT: return "timed out";
+    case EXSUM_EBUSY: return "busy";
+    default: return "unknown status";
+    }
+}
+
+int exsum_last_cuda_error(void) { return g_last_cuda_error; }
+
+int exsum_out_dtype(int dtype)
+{
+    if (dtype < EXSUM_I32 || dtype > EXSUM_BF16) return -1;
+    return dtype == EXSUM_BF16 ? EXSUM_F32 : dtype;
+}
+
+size_t exsum_dtype_size(int dtype)
+{
+    switch (dtype) {
+    case EXSUM_I32: return 4;
+    case EXSUM_I64: return 8;
+    case EXSUM_F32: return 4;
+    case EXSUM_BF16: return 2;
+    default: return 0;
+    }
+}
+
+size_t exsum_workspace_bytes(int d, const int64_t *shape, const int64_t *k, int op, int dtype,
+                             int excluded, int *status)
+{
+    int rc = validate(d, shape, k, op, dtype);
+    size_t need = 0;
+    if (!rc) rc = run(excluded ? 1 : 0, nullptr, nullptr, d, shape, k, op, dtype, nullptr, 0, nullptr, &need);
+    if (status) *status = rc;
+    return rc ? 0 : need;
+}
+
+int exsum_included(const void *in, void *out, int d, const int64_t *shape, const int64_t *k, int op,
+                   int dtype, void *stream)
+{
+    return call_cached(0, in, out, d, shape, k, op, dtype, stream);
+}
+
+int exsum_excluded(const void *in, void *out, int d, const int64_t *shape, const int64_t *k, int op,
+                   int dtype, void *stream)
+{
+    return call_cached(1, in, out, d, shape, k, op, dtype, stream);
+}
+
+int exsum_included_ws(const void *in, void *out, int d, const int64_t *shape, const int64_t *k,
+                      int op, int dtype, void *workspace, size_t workspace_bytes, void *stream)
+{
+    int rc = validate(d, shape, k, op, dtype);
+    if (rc) return rc;
+    if (!in || !out) return EXSUM_EINVAL;
+    return run(0, in, out, d, shape, k, op, dtype, workspace, workspace_bytes, stream, nullptr);
+}
+
+int exsum_excluded_ws(const void *in, void *out, int d, const int64_t *shape, const int64_t *k,
+                      int op, int dtype, void *workspace, size_t workspace_bytes, void *stream)
+{
+    int rc = validate(d, shape, k, op, dtype);
+    if (rc) return rc;
+    if (!in || !out) return EXSUM_EINVAL;
+    return run(1, in, out, d, shape, k, op, dtype, workspace, workspace_bytes, stream, nullptr);
+}
+
+int exsum_release_cached_workspace(void)
+{
+    std::lock_guard<std::mutex> lock(g_cache_mu);
+    cudaError_t e = cudaDeviceSynchronize();
+    int cur = 0;
+    cudaGetDevice(&cur);
+    for (auto &kv : g_cache) {
+        if (kv.second.ptr) {
+            cudaSetDevice(kv.first.first);
+            cudaError_t f = cudaFree(kv.second.ptr);
+            if (e == cudaSuccess) e = f;
+        }
+    }
+    cudaSetDevice(cur);
+    g_cache.clear();
+    if (e != cudaSuccess) {
+        g_last_cuda_error = (int)e;
+        return EXSUM_ECUDA;
+    }
+    return EXSUM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,308 @@
+// kernels_lines.cuh -- line kernels of the GPU path.
+//
+// Every pass of BDBS and box-complement works on "lines": the rows of a
+// tensor along one dimension (Sec. 2, "a (tensor) row").  A tensor is seen
+// as a 3-D view [O, n, I]: O outer positions, the dimension of length n
+// being processed, and I inner positions (I = 1 when the dimension is the
+// contiguous one).  Element x of line (o, i) sits at o*n*I + x*I + i.
+//
+// Kernels here:
+//   k_inc_lines    BDBS-Along-Dim: the included sum of window k along each
+//                  line, by the k-blocked prefix and suffix scans and the
+//                  combine step of BDBS-1D (Sec. 3).
+//   k_reduce_seg   Reductions of fixed-length segments of each line (the
+//                  totals the dimension-reduction steps of Sec. 5 carry).
+//   k_sum_segs_*   Reduction of segment totals to column totals.
+//   k_carry_*      Per-segment carries of the prefix/suffix along dim 1.
+//   k_exline       Prefix-Along-Dim / Suffix-Along-Dim along dimension 1
+//                  fused with Add-Contribution (Sec. 5), per segment.
+#pragma once
+
+#include "monoid.cuh"
+
+namespace exsum {
+
+// ---------------------------------------------------------------------------
+// Block-wide exclusive prefix and exclusive suffix of one value per thread.
+// Every thread of the block must call it.
+// ---------------------------------------------------------------------------
+template <class M, int NT>
+__device__ __forceinline__ void block_exscan_both(typename M::acc_t v, typename M::acc_t &pre,
+                                                  typename M::acc_t &suf)
+{
+    using A = typename M::acc_t;
+    constexpr int NW = NT / 32;
+    __shared__ A wtot[NW];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    A inc = v;
+#pragma unroll
+    for (int dl = 1; dl < 32; dl <<= 1) {
+        A o = shfl_up(inc, dl);
+        if (lane >= dl) inc = M::op(o, inc);
+    }
+    A sinc = v;
+#pragma unroll
+    for (int dl = 1; dl < 32; dl <<= 1) {
+        A o = shfl_down(sinc, dl);
+        if (lane + dl < 32) sinc = M::op(sinc, o);
+    }
+    if (lane == 31) wtot[warp] = inc;
+    __syncthreads();
+    A wpre = M::id(), wsuf = M::id();
+    for (int w = 0; w < warp; ++w) wpre = M::op(wpre, wtot[w]);
+    for (int w = NW - 1; w > warp; --w) wsuf = M::op(wtot[w], wsuf);
+    A ex = shfl_up(inc, 1);
+    if (lane == 0) ex = M::id();
+    A sx = shfl_down(sinc, 1);
+    if (lane == 31) sx = M::id();
+    pre = M::op(wpre, ex);
+    suf = M::op(sx, wsuf);
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// BDBS-Along-Dim for one chunk of one line per thread.
+//
+// The thread produces outputs x in [r0, min(r0+Lc, n)) of its line and reads
+// inputs up to x+k-1 (elements past n are the identity: the clipped box of
+// Sec. 2 / the identity padding of the Sec. 3 footnote).  Blocks of length k
+// start at r0.  For x in block b the window [x, x+k) is the suffix of block b
+// from x (Range-Suffix-Row) followed by the prefix of block b+1 up to x+k-1
+// (Range-Prefix-Row); a block start takes its whole block (Combine-Along-Row,
+// Lemma "Correctness in 1D").  The suffix of the current block is held in k
+// per-thread slots (shared memory, or global scratch for large k); the next
+// block's prefix is a running register value, and its elements replace the
+// consumed suffix slots as they stream in.
+// ---------------------------------------------------------------------------
+template <class M, class SIn, class SOut>
+__global__ void __launch_bounds__(128)
+k_inc_lines(const SIn *__restrict__ in, SOut *__restrict__ out, int64_t O, int64_t n, int64_t I,
+            int64_t k, int64_t Lc, int64_t nchunks, typename M::acc_t *__restrict__ gslots)
+{
+    using A = typename M::acc_t;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int64_t total = O * nchunks * I;
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= total) return;
+    const int64_t i = gid % I;
+    const int64_t rest = gid / I;
+    const int64_t ch = rest % nchunks;
+    const int64_t o = rest / nchunks;
+    const int64_t base = o * n * I + i;
+    A *slot;
+    int64_t ss;
+    if (gslots) {
+        slot = gslots + gid;
+        ss = total;
+    } else {
+        slot = reinterpret_cast<A *>(smem_raw) + threadIdx.x;
+        ss = blockDim.x;
+    }
+    const int64_t r0 = ch * Lc;
+    const int64_t rend = (r0 + Lc < n) ? r0 + Lc : n;
+
+    // Block 0: load, then suffix scan in place.
+    for (int64_t j = 0; j < k; ++j) {
+        const int64_t x = r0 + j;
+        slot[j * ss] = x < n ? M::get(in[base + x * I]) : M::id();
+    }
+    for (int64_t j = k - 2; j >= 0; --j) slot[j * ss] = M::op(slot[j * ss], slot[(j + 1) * ss]);
+
+    for (int64_t sb = r0; sb < rend; sb += k) {
+        out[base + sb * I] = M::template put<SOut>(slot[0]);
+        A p = M::id();
+        const int64_t jmax = (rend - sb - 1 < k - 1) ? rend - sb - 1 : k - 1;  // outputs left in block
+        const bool more = sb + k < rend;
+#pragma unroll 4
+        for (int64_t j = 0; j < k - 1; ++j) {
+            if (j >= jmax && !more) break;
+            const int64_t xn = sb + k + j;
+            const A v = xn < n ? M::get(in[base + xn * I]) : M::id();
+            p = M::op(p, v);
+            if (j < jmax) out[base + (sb + 1 + j) * I] = M::template put<SOut>(M::op(slot[(j + 1) * ss], p));
+            slot[j * ss] = v;
+        }
+        if (more) {
+            const int64_t xl = sb + 2 * k - 1;
+            slot[(k - 1) * ss] = xl < n ? M::get(in[base + xl * I]) : M::id();
+            for (int64_t j = k - 2; j >= 0; --j) slot[j * ss] = M::op(slot[j * ss], slot[(j + 1) * ss]);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Segment reductions along dimension 1 of a view [n1, Mc] (row-major, Mc
+// columns).  Segment s covers rows [s*L, min(s*L+L, n1)).  R[s][c] is the
+// whole segment; Rt[s][c] (if non-null) the segment from offset r on.
+// ---------------------------------------------------------------------------
+template <class M, class SIn>
+__global__ void __launch_bounds__(256)
+k_reduce_seg(const SIn *__restrict__ X, typename M::car_t *__restrict__ R,
+             typename M::car_t *__restrict__ Rt, int64_t n1, int64_t Mc, int64_t L, int64_t S,
+             int64_t r)
+{
+    using A = typename M::acc_t;
+    using C = typename M::car_t;
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= S * Mc) return;
+    const int64_t c = gid % Mc, s = gid / Mc;
+    const int64_t y0 = s * L;
+    const int64_t y1 = (y0 + L < n1) ? y0 + L : n1;
+    const int64_t ys = (y0 + r < y1) ? y0 + r : y1;
+    A head = M::id(), tail = M::id();
+#pragma unroll 4
+    for (int64_t y = y0; y < ys; ++y) head = M::op(head, M::get(X[y * Mc + c]));
+#pragma unroll 4
+    for (int64_t y = ys; y < y1; ++y) tail = M::op(tail, M::get(X[y * Mc + c]));
+    R[gid] = M::template put<C>(M::op(head, tail));
+    if (Rt) Rt[gid] = M::template put<C>(tail);
+}
+
+// Column totals G[c] = (+)_s R[s][c]; one thread per column.
+template <class M>
+__global__ void __launch_bounds__(256)
+k_sum_segs_col(const typename M::car_t *__restrict__ R, typename M::car_t *__restrict__ G,
+               int64_t Mc, int64_t S)
+{
+    using A = typename M::acc_t;
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= Mc) return;
+    A acc = M::id();
+    for (int64_t s = 0; s < S; ++s) acc = M::op(acc, M::get(R[s * Mc + c]));
+    G[c] = M::template put<typename M::car_t>(acc);
+}
+
+// Column totals with one block per column (few columns, many segments).
+template <class M, int NT>
+__global__ void __launch_bounds__(NT)
+k_sum_segs_blk(const typename M::car_t *__restrict__ R, typename M::car_t *__restrict__ G,
+               int64_t Mc, int64_t S)
+{
+    using A = typename M::acc_t;
+    const int64_t c = blockIdx.x;
+    A acc = M::id();
+    for (int64_t s = threadIdx.x; s < S; s += NT) acc = M::op(acc, M::get(R[s * Mc + c]));
+    A pre, suf;
+    block_exscan_both<M, NT>(acc, pre, suf);
+    if (threadIdx.x == NT - 1) G[c] = M::template put<typename M::car_t>(M::op(pre, acc));
+}
+
+// ---------------------------------------------------------------------------
+// Carries of the dimension-1 prefix/suffix, per segment s and column c:
+//   Pc[s] = (+) of segments before s                       (exclusive prefix)
+//   W[s]  = (+) of rows >= (s+1)*L + k1                     (suffix past the
+//           target window of segment s); with q = s + qoff, qoff = 1 + k1/L,
+//           r = k1 mod L, this is Rt[q] (+) (+)_{s' > q} R[s'].
+//   Q[s]  = Pc[s] (+) W[s] (+) T[c]   (T: the lower-dimensional excluded sum
+//           of the column totals, or the identity)
+// ---------------------------------------------------------------------------
+template <class M>
+__global__ void __launch_bounds__(256)
+k_carry_col(const typename M::car_t *__restrict__ R, const typename M::car_t *__restrict__ Rt,
+            const typename M::car_t *__restrict__ T, typename M::car_t *__restrict__ Q, int64_t Mc,
+            int64_t S, int64_t qoff)
+{
+    using A = typename M::acc_t;
+    using C = typename M::car_t;
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= Mc) return;
+    // Backward: suffix totals SR[s] = (+)_{s' >= s} R[s'], parked in Q.
+    A acc = M::id();
+    for (int64_t s = S - 1; s >= 0; --s) {
+        acc = M::op(M::get(R[s * Mc + c]), acc);
+        Q[s * Mc + c] = M::template put<C>(acc);
+    }
+    const A tc = T ? M::get(T[c]) : M::id();
+    A pc = M::id();
+    for (int64_t s = 0; s < S; ++s) {
+        const int64_t q = s + qoff;
+        A w = M::id();
+        if (q < S) {
+            w = M::get(Rt[q * Mc + c]);
+            if (q + 1 < S) w = M::op(w, M::get(Q[(q + 1) * Mc + c]));  // SR[q+1], q+1 > s: not yet overwritten
+        }
+        const A rs = M::get(R[s * Mc + c]);
+        Q[s * Mc + c] = M::template put<C>(M::op(M::op(pc, w), tc));
+        pc = M::op(pc, rs);
+    }
+}
+
+// Same carries with one block per column (many segments, few columns).
+// SR is a scratch array of S*Mc carries.
+template <class M, int NT>
+__global__ void __launch_bounds__(NT)
+k_carry_blk(const typename M::car_t *__restrict__ R, const typename M::car_t *__restrict__ Rt,
+            const typename M::car_t *__restrict__ T, typename M::car_t *__restrict__ Q,
+            typename M::car_t *__restrict__ SR, int64_t Mc, int64_t S, int64_t qoff)
+{
+    using A = typename M::acc_t;
+    using C = typename M::car_t;
+    const int64_t c = blockIdx.x;
+    const int64_t per = (S + NT - 1) / NT;
+    const int64_t sb = threadIdx.x * per;
+    const int64_t se = (sb + per < S) ? sb + per : S;
+    A tot = M::id();
+    for (int64_t s = sb; s < se; ++s) tot = M::op(tot, M::get(R[s * Mc + c]));
+    A pre, suf;
+    block_exscan_both<M, NT>(tot, pre, suf);
+    A acc = suf;
+    for (int64_t s = se - 1; s >= sb; --s) {
+        acc = M::op(M::get(R[s * Mc + c]), acc);
+        SR[s * Mc + c] = M::template put<C>(acc);
+    }
+    __syncthreads();
+    const A tc = T ? M::get(T[c]) : M::id();
+    A pc = pre;
+    for (int64_t s = sb; s < se; ++s) {
+        const int64_t q = s + qoff;
+        A w = M::id();
+        if (q < S) {
+            w = M::get(Rt[q * Mc + c]);
+            if (q + 1 < S) w = M::op(w, M::get(SR[(q + 1) * Mc + c]));
+        }
+        Q[s * Mc + c] = M::template put<C>(M::op(M::op(pc, w), tc));
+        pc = M::op(pc, M::get(R[s * Mc + c]));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Dimension-1 step of box-complement for one segment of one column
+// (view [n1, Mc]; segment s = rows [s*L, s*L+L)).  For x1 = s*L + t:
+//   out[x1][c] = Q (+) (+)_{u < t} H[s*L+u][c]              prefix, x1 excluded
+//                  (+) (+)_{v = t}^{L-1} H[s*L+k1+v][c]     suffix from x1+k1
+// Q carries the rest (segments before, rows past the target window, and the
+// lower-dimensional excluded sum).  This is Prefix-Along-Dim and
+// Suffix-Along-Dim along dimension 1 with the two Add-Contribution offsets
+// (-1 and +k1) of Fig. "exsum-code-full", evaluated per output instead of
+// per input.  The exclusive prefix is kept in L registers.
+// ---------------------------------------------------------------------------
+template <class M, class SIn, class SOut, int L>
+__global__ void __launch_bounds__(128)
+k_exline(const SIn *__restrict__ H, const typename M::car_t *__restrict__ Q, int64_t qs,
+         SOut *__restrict__ out, int64_t n1, int64_t Mc, int64_t k1, int64_t S)
+{
+    using A = typename M::acc_t;
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= S * Mc) return;
+    const int64_t c = gid % Mc, s = gid / Mc;
+    const int64_t s0 = s * L;
+    A P[L];
+    A acc = M::id();
+#pragma unroll
+    for (int t = 0; t < L; ++t) {
+        P[t] = acc;
+        const int64_t y = s0 + t;
+        if (y < n1) acc = M::op(acc, M::get(H[y * Mc + c]));
+    }
+    const A q = Q ? M::get(Q[s * qs + c]) : M::id();
+    A sacc = M::id();
+#pragma unroll
+    for (int t = L - 1; t >= 0; --t) {
+        const int64_t y = s0 + k1 + t;
+        if (y < n1) sacc = M::op(M::get(H[y * Mc + c]), sacc);
+        const int64_t x = s0 + t;
+        if (x < n1) out[x * Mc + c] = M::template put<SOut>(M::op(M::op(q, P[t]), sacc));
+    }
+}
+
+}  // namespace exsum

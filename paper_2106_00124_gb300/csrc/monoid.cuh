@@ -1,0 +1,172 @@
+// monoid.cuh -- element types and operators of the GPU path.
+//
+// The paper states every algorithm over a monoid (S, (+), e) (Sec. 1);
+// box-complement also regroups operands across regions, so the operator must
+// be commutative as well.  This library provides + and max:
+//
+//   dtype  op   input      accumulate             big intermediates  carries   output
+//   I32    +    int32      int32, wraps mod 2^32  int32              int32     int32
+//   I64    +    int64      int64, wraps mod 2^64  int64              int64     int64
+//   F32    +    fp32       fp32 pair (hi, lo)     fp32 (hi+lo)       fp32 pair fp32
+//   BF16   +    bf16 bits  fp32 pair (hi, lo)     fp32 (hi+lo)       fp32 pair fp32
+//   *      max  as above   the input's value type, identity INT_MIN / -inf
+//
+// Integer + and max are exact under any regrouping, so integer and max
+// results are bit-exact.  Floating-point + carries its running sums as an
+// unevaluated pair hi + lo (Knuth's TwoSum), so long reductions -- carries
+// along dimension 1, column totals, the recursion's totals -- lose almost
+// nothing to rounding; the short window sums of the big intermediate tensor
+// are rounded to fp32 once each.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace exsum {
+
+enum { OP_ADD = 0, OP_MAX = 1 };
+
+// A compensated fp32 value: the exact value is hi + lo.
+struct __align__(8) f2 {
+    float hi, lo;
+};
+
+// Double-float addition: TwoSum of the high parts (Knuth), the low parts
+// folded into the error term, then a FastTwoSum renormalisation.  Written
+// with explicit round-to-nearest intrinsics so that the compiler cannot
+// contract or regroup it.
+__device__ __forceinline__ f2 f2_add(f2 a, f2 b)
+{
+    const float s = __fadd_rn(a.hi, b.hi);
+    const float bv = __fsub_rn(s, a.hi);
+    const float av = __fsub_rn(s, bv);
+    const float err = __fadd_rn(__fsub_rn(a.hi, av), __fsub_rn(b.hi, bv));
+    const float lo = __fadd_rn(err, __fadd_rn(a.lo, b.lo));
+    const float hi = __fadd_rn(s, lo);
+    f2 r;
+    r.hi = hi;
+    r.lo = __fsub_rn(lo, __fsub_rn(hi, s));
+    return r;
+}
+
+__device__ __forceinline__ float bf16_bits_to_float(uint16_t b)
+{
+    return __uint_as_float(((uint32_t)b) << 16);
+}
+
+// --- integer + (wrapping) -----------------------------------------------------
+template <class T, class U>
+struct MonIntAdd {
+    using in_t = T;
+    using out_t = T;
+    using acc_t = T;
+    using car_t = T;
+    static constexpr bool compensated = false;
+    __device__ __forceinline__ static acc_t id() { return (T)0; }
+    __device__ __forceinline__ static acc_t op(acc_t a, acc_t b) { return (T)((U)a + (U)b); }
+    __device__ __forceinline__ static acc_t get(T v) { return v; }
+    template <class S>
+    __device__ __forceinline__ static S put(acc_t a) { return a; }
+};
+
+// --- integer max ---------------------------------------------------------------
+template <class T, long long MINV>
+struct MonIntMax {
+    using in_t = T;
+    using out_t = T;
+    using acc_t = T;
+    using car_t = T;
+    static constexpr bool compensated = false;
+    __device__ __forceinline__ static acc_t id() { return (T)MINV; }
+    __device__ __forceinline__ static acc_t op(acc_t a, acc_t b) { return a > b ? a : b; }
+    __device__ __forceinline__ static acc_t get(T v) { return v; }
+    template <class S>
+    __device__ __forceinline__ static S put(acc_t a) { return a; }
+};
+
+// --- floating-point + with compensated accumulation -----------------------------
+template <class IN>
+struct MonFloatAdd {
+    using in_t = IN;        // float or uint16_t (bf16 bits)
+    using out_t = float;
+    using acc_t = f2;
+    using car_t = f2;
+    static constexpr bool compensated = true;
+    __device__ __forceinline__ static acc_t id() { f2 z; z.hi = 0.f; z.lo = 0.f; return z; }
+    __device__ __forceinline__ static acc_t op(acc_t a, acc_t b) { return f2_add(a, b); }
+    __device__ __forceinline__ static acc_t get(float v) { f2 r; r.hi = v; r.lo = 0.f; return r; }
+    __device__ __forceinline__ static acc_t get(uint16_t v) { return get(bf16_bits_to_float(v)); }
+    __device__ __forceinline__ static acc_t get(f2 v) { return v; }
+    template <class S>
+    __device__ __forceinline__ static S put(acc_t a);
+};
+template <>
+template <>
+__device__ __forceinline__ float MonFloatAdd<float>::put<float>(f2 a) { return __fadd_rn(a.hi, a.lo); }
+template <>
+template <>
+__device__ __forceinline__ f2 MonFloatAdd<float>::put<f2>(f2 a) { return a; }
+template <>
+template <>
+__device__ __forceinline__ float MonFloatAdd<uint16_t>::put<float>(f2 a) { return __fadd_rn(a.hi, a.lo); }
+template <>
+template <>
+__device__ __forceinline__ f2 MonFloatAdd<uint16_t>::put<f2>(f2 a) { return a; }
+
+// --- floating-point max -----------------------------------------------------------
+template <class IN>
+struct MonFloatMax {
+    using in_t = IN;
+    using out_t = float;
+    using acc_t = float;
+    using car_t = float;
+    static constexpr bool compensated = false;
+    __device__ __forceinline__ static acc_t id() { return -__int_as_float(0x7f800000); }
+    __device__ __forceinline__ static acc_t op(acc_t a, acc_t b) { return fmaxf(a, b); }
+    __device__ __forceinline__ static acc_t get(float v) { return v; }
+    __device__ __forceinline__ static acc_t get(uint16_t v) { return bf16_bits_to_float(v); }
+    template <class S>
+    __device__ __forceinline__ static S put(acc_t a) { return a; }
+};
+
+using M_I32_ADD = MonIntAdd<int32_t, uint32_t>;
+using M_I64_ADD = MonIntAdd<int64_t, uint64_t>;
+using M_I32_MAX = MonIntMax<int32_t, (long long)INT32_MIN>;
+using M_I64_MAX = MonIntMax<int64_t, (long long)INT64_MIN>;
+using M_F32_ADD = MonFloatAdd<float>;
+using M_F32_MAX = MonFloatMax<float>;
+using M_BF16_ADD = MonFloatAdd<uint16_t>;
+using M_BF16_MAX = MonFloatMax<uint16_t>;
+
+// --- warp shuffles of accumulator values ---------------------------------------------
+__device__ __forceinline__ int32_t shfl_up(int32_t v, int dl) { return __shfl_up_sync(0xffffffffu, v, dl); }
+__device__ __forceinline__ int64_t shfl_up(int64_t v, int dl)
+{
+    return (int64_t)__shfl_up_sync(0xffffffffu, (long long)v, dl);
+}
+__device__ __forceinline__ float shfl_up(float v, int dl) { return __shfl_up_sync(0xffffffffu, v, dl); }
+__device__ __forceinline__ f2 shfl_up(f2 v, int dl)
+{
+    f2 r;
+    r.hi = __shfl_up_sync(0xffffffffu, v.hi, dl);
+    r.lo = __shfl_up_sync(0xffffffffu, v.lo, dl);
+    return r;
+}
+__device__ __forceinline__ int32_t shfl_down(int32_t v, int dl)
+{
+    return __shfl_down_sync(0xffffffffu, v, dl);
+}
+__device__ __forceinline__ int64_t shfl_down(int64_t v, int dl)
+{
+    return (int64_t)__shfl_down_sync(0xffffffffu, (long long)v, dl);
+}
+__device__ __forceinline__ float shfl_down(float v, int dl) { return __shfl_down_sync(0xffffffffu, v, dl); }
+__device__ __forceinline__ f2 shfl_down(f2 v, int dl)
+{
+    f2 r;
+    r.hi = __shfl_down_sync(0xffffffffu, v.hi, dl);
+    r.lo = __shfl_down_sync(0xffffffffu, v.lo, dl);
+    return r;
+}
+
+}  // namespace exsum

@@ -1,0 +1,262 @@
+// pipeline.cuh -- pass sequences of BDBS (included sums) and box-complement
+// (excluded sums) for one monoid, on one CUDA stream.
+//
+// The same code runs in two modes: a dry run that only measures the
+// workspace, and a real run that carves the workspace identically and
+// launches the kernels.  Keeping both in one function keeps the workspace
+// figure and the launches in step.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include "kernels_lines.cuh"
+
+namespace exsum {
+
+// Status codes, mirrored from include/exsum.h (kept numerically identical).
+enum { ST_OK = 0, ST_EINVAL = -1, ST_ENOMEM = -2, ST_EUNSUP = -3, ST_ECUDA = -4 };
+
+struct Ctx {
+    char *base = nullptr;   // workspace (device)
+    size_t cap = 0;         // workspace bytes available
+    size_t off = 0;         // bytes carved so far
+    bool dry = true;        // measure only
+    cudaStream_t stream = 0;
+    int status = ST_OK;
+    cudaError_t cuda_err = cudaSuccess;
+
+    template <class T>
+    T *take(int64_t count)
+    {
+        const size_t bytes = ((size_t)count * sizeof(T) + 255) & ~(size_t)255;
+        T *p = dry ? nullptr : reinterpret_cast<T *>(base + off);
+        off += bytes;
+        if (!dry && off > cap && status == ST_OK) status = ST_ENOMEM;
+        return p;
+    }
+    bool ok() const { return status == ST_OK; }
+    void check_launch()
+    {
+        if (dry) return;
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess && status == ST_OK) {
+            status = ST_ECUDA;
+            cuda_err = e;
+        }
+    }
+};
+
+static inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+template <class M>
+struct Pipe {
+    using A = typename M::acc_t;
+    using IN = typename M::in_t;
+    using OUT = typename M::out_t;
+    using CAR = typename M::car_t;
+
+    static constexpr int EXL = 32;            // segment length of the dimension-1 step
+    static constexpr int INC_THREADS = 128;
+    static constexpr size_t SLOT_SMEM_MAX = 96 * 1024;
+
+    // ---- BDBS-Along-Dim over a view [O, n, I] -------------------------------------
+    template <class SIn, class SOut>
+    static void inc_pass(Ctx &cx, const SIn *src, SOut *dst, int64_t O, int64_t n, int64_t I,
+                         int64_t k)
+    {
+        if (!cx.ok()) return;
+        int threads = INC_THREADS;
+        while (threads > 32 && (size_t)k * threads * sizeof(A) > SLOT_SMEM_MAX) threads >>= 1;
+        const bool global_slots = (size_t)k * threads * sizeof(A) > SLOT_SMEM_MAX;
+        int64_t Lc = 64 > 2 * k ? 64 : 2 * k;
+        if (global_slots && Lc < 4 * k) Lc = 4 * k;
+        if (Lc > n) Lc = n;
+        const int64_t nchunks = cdiv(n, Lc);
+        const int64_t total = O * nchunks * I;
+        A *gslots = global_slots ? cx.take<A>(total * k) : nullptr;
+        if (cx.dry || !cx.ok()) return;
+        const size_t smem = global_slots ? 0 : (size_t)k * threads * sizeof(A);
+        auto kern = k_inc_lines<M, SIn, SOut>;
+        if (smem > 48 * 1024)
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        kern<<<(unsigned)cdiv(total, threads), threads, smem, cx.stream>>>(src, dst, O, n, I, k, Lc,
+                                                                           nchunks, gslots);
+        cx.check_launch();
+    }
+
+    // ---- column totals over dimension 1 of a view [n1, Mc] ----------------------------
+    template <class SIn>
+    static void colsum(Ctx &cx, const SIn *X, CAR *G, int64_t n1, int64_t Mc)
+    {
+        if (!cx.ok()) return;
+        int64_t S = cdiv(65536, Mc);
+        if (S > n1) S = n1;
+        if (S < 1) S = 1;
+        const int64_t L = cdiv(n1, S);
+        S = cdiv(n1, L);
+        if (S == 1) {
+            if (cx.dry) return;
+            k_reduce_seg<M, SIn><<<(unsigned)cdiv(Mc, 256), 256, 0, cx.stream>>>(X, G, nullptr, n1,
+                                                                                  Mc, L, 1, 0);
+            cx.check_launch();
+            return;
+        }
+        CAR *Rx = cx.take<CAR>(S * Mc);
+        if (cx.dry || !cx.ok()) return;
+        k_reduce_seg<M, SIn><<<(unsigned)cdiv(S * Mc, 256), 256, 0, cx.stream>>>(X, Rx, nullptr, n1,
+                                                                                  Mc, L, S, 0);
+        cx.check_launch();
+        if (Mc >= 1024)
+            k_sum_segs_col<M><<<(unsigned)cdiv(Mc, 256), 256, 0, cx.stream>>>(Rx, G, Mc, S);
+        else
+            k_sum_segs_blk<M, 256><<<(unsigned)Mc, 256, 0, cx.stream>>>(Rx, G, Mc, S);
+        cx.check_launch();
+    }
+
+    // ---- dimension-1 step: prefix/suffix along dim 1 + contributions --------------------
+    template <class SH, class SOut>
+    static void exline_stage(Ctx &cx, const SH *H, const CAR *T, SOut *out, int64_t n1,
+                             int64_t Mc, int64_t k1)
+    {
+        if (!cx.ok()) return;
+        const int64_t S = cdiv(n1, EXL);
+        const CAR *Q = T;
+        int64_t qs = 0;
+        if (S > 1) {
+            CAR *R = cx.take<CAR>(S * Mc);
+            CAR *Rt = cx.take<CAR>(S * Mc);
+            CAR *Qb = cx.take<CAR>(S * Mc);
+            const bool blk = S > 64 && Mc < 4096;
+            CAR *SR = blk ? cx.take<CAR>(S * Mc) : nullptr;
+            if (cx.dry || !cx.ok()) return;
+            k_reduce_seg<M, SH><<<(unsigned)cdiv(S * Mc, 256), 256, 0, cx.stream>>>(
+                H, R, Rt, n1, Mc, EXL, S, k1 % EXL);
+            cx.check_launch();
+            const int64_t qoff = 1 + k1 / EXL;
+            if (blk)
+                k_carry_blk<M, 1024><<<(unsigned)Mc, 1024, 0, cx.stream>>>(R, Rt, T, Qb, SR, Mc, S,
+                                                                           qoff);
+            else
+                k_carry_col<M><<<(unsigned)cdiv(Mc, 256), 256, 0, cx.stream>>>(R, Rt, T, Qb, Mc, S,
+                                                                                qoff);
+            cx.check_launch();
+            Q = Qb;
+            qs = Mc;
+        }
+        if (cx.dry || !cx.ok()) return;
+        k_exline<M, SH, SOut, EXL><<<(unsigned)cdiv(S * Mc, 128), 128, 0, cx.stream>>>(
+            H, Q, qs, out, n1, Mc, k1, S);
+        cx.check_launch();
+    }
+
+    // ---- included sums: BDBS along every dimension ---------------------------------------
+    template <class SIn, class SOut>
+    static void included(Ctx &cx, const SIn *X, SOut *out, int d, const int64_t *n,
+                         const int64_t *k)
+    {
+        int64_t N = 1;
+        for (int i = 0; i < d; ++i) N *= n[i];
+        int dims[16];
+        int P = 0;
+        for (int j = d - 1; j >= 0; --j)
+            if (k[j] > 1) dims[P++] = j;
+        if (P == 0) dims[P++] = d - 1;  // a k = 1 pass converts the input type
+        SOut *B = P > 1 ? cx.take<SOut>(N) : nullptr;
+        const void *cur = X;
+        for (int p = 0; p < P; ++p) {
+            const int j = dims[p];
+            int64_t O = 1, I = 1;
+            for (int m = 0; m < j; ++m) O *= n[m];
+            for (int m = j + 1; m < d; ++m) I *= n[m];
+            SOut *dst = ((P - 1 - p) % 2 == 0) ? out : B;
+            if (p == 0)
+                inc_pass<SIn, SOut>(cx, (const SIn *)cur, dst, O, n[j], I, k[j]);
+            else
+                inc_pass<SOut, SOut>(cx, (const SOut *)cur, dst, O, n[j], I, k[j]);
+            cur = dst;
+        }
+    }
+
+    // ---- excluded sums: box-complement, one dimension-reduction step per level ---------------
+    //
+    // Level with input X of shape n[0..d-1]:
+    //   H  = included sum of X along dimensions 2..d            (BDBS-Along-Dim)
+    //   G  = total of X over dimension 1                          (dimension reduction)
+    //   T  = excluded sum of G with box k[1..d-1]                 (next level)
+    //   out[x] = prefix of H along dim 1 before x_1 (+) suffix of H along dim 1 from
+    //            x_1+k_1 (+) T[x_2..x_d]
+    // which is the two regions of step 1 in Corollary "Excluded-sum Components" plus
+    // the regions of steps 2..d (all of which range over the whole of dimension 1).
+    template <class SIn, class SOut>
+    static void excluded(Ctx &cx, const SIn *X, SOut *out, int d, const int64_t *n,
+                         const int64_t *k)
+    {
+        if (!cx.ok()) return;
+        int64_t N = 1;
+        for (int i = 0; i < d; ++i) N *= n[i];
+        const int64_t M1 = N / n[0];
+        if (d == 1) {
+            exline_stage<SIn, SOut>(cx, X, nullptr, out, n[0], 1, k[0]);
+            return;
+        }
+        int dims[16];
+        int P = 0;
+        for (int j = d - 1; j >= 1; --j)
+            if (k[j] > 1) dims[P++] = j;
+        SOut *B = P > 0 ? cx.take<SOut>(N) : nullptr;
+        CAR *G = cx.take<CAR>(M1);
+        CAR *T = cx.take<CAR>(M1);
+        // H: BDBS along dims d..2, ping-ponging between out and B and ending in B.
+        const void *cur = X;
+        for (int p = 0; p < P; ++p) {
+            const int j = dims[p];
+            int64_t O = 1, I = 1;
+            for (int m = 0; m < j; ++m) O *= n[m];
+            for (int m = j + 1; m < d; ++m) I *= n[m];
+            SOut *dst = ((P - 1 - p) % 2 == 0) ? B : out;
+            if (p == 0)
+                inc_pass<SIn, SOut>(cx, (const SIn *)cur, dst, O, n[j], I, k[j]);
+            else
+                inc_pass<SOut, SOut>(cx, (const SOut *)cur, dst, O, n[j], I, k[j]);
+            cur = dst;
+        }
+        colsum<SIn>(cx, X, G, n[0], M1);
+        excluded<CAR, CAR>(cx, G, T, d - 1, n + 1, k + 1);
+        if (P > 0)
+            exline_stage<SOut, SOut>(cx, B, T, out, n[0], M1, k[0]);
+        else
+            exline_stage<SIn, SOut>(cx, X, T, out, n[0], M1, k[0]);
+    }
+
+    // ---- entry -----------------------------------------------------------------------------
+    static int run(int excluded_sum, const void *in, void *out, int d, const int64_t *n,
+                   const int64_t *k, void *ws, size_t ws_bytes, cudaStream_t stream,
+                   size_t *ws_needed, cudaError_t *cuda_err)
+    {
+        Ctx cx;
+        cx.dry = true;
+        if (excluded_sum)
+            excluded<IN, OUT>(cx, nullptr, nullptr, d, n, k);
+        else
+            included<IN, OUT>(cx, nullptr, nullptr, d, n, k);
+        const size_t need = cx.off;
+        if (ws_needed) *ws_needed = need;
+        if (!in) return ST_OK;  // size query only
+        if (need > ws_bytes || (need > 0 && !ws)) return ST_ENOMEM;
+        Ctx rx;
+        rx.dry = false;
+        rx.base = (char *)ws;
+        rx.cap = ws_bytes;
+        rx.stream = stream;
+        if (excluded_sum)
+            excluded<IN, OUT>(rx, (const IN *)in, (OUT *)out, d, n, k);
+        else
+            included<IN, OUT>(rx, (const IN *)in, (OUT *)out, d, n, k);
+        if (cuda_err) *cuda_err = rx.cuda_err;
+        return rx.status;
+    }
+};
+
+}  // namespace exsum
