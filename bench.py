@@ -1,0 +1,439 @@
+#!/usr/bin/env python
+"""Benchmark of the excluded-sum hot path on GB300.
+
+One step = one strong excluded sum (box-complement) of a synthetic tensor
+through the C ABI.  The default workload is the 256^3 fp32 tensor with
+values uniform in [-1, 1), box k = (8, 8, 8), operator +.  Prints ONE JSON
+line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+  python bench.py --impl reference ...   # the CPU oracle, timed on host cores
+
+Timing: each step is bracketed by CUDA events on the stream the library
+launches on; between steps a 256 MiB buffer is written to flush the 129 MB
+L2, outside the timed spans.  `value` sums the K step spans; the per-kernel
+roofline comes from the library's launch trace over the same timed region.
+"""
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "excluded-sum Gelem/s"
+UNIT = "Gelem/s"
+DEFAULT_WORKLOAD = "d3_256cube_f32_add_k8"
+FLUSH_BYTES = 256 << 20
+FALLBACK_HBM_GBS = 6800.0
+
+BYTES = {"i32": 4, "i64": 8, "f32": 4, "bf16": 2}
+OUT_BYTES = {"i32": 4, "i64": 8, "f32": 4, "bf16": 4}
+
+
+def parse_args(argv=None):
+    p = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawTextHelpFormatter)
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=2000)
+    p.add_argument("--warmup", type=int, default=20)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args(argv)
+
+
+# ---- multi-rank plumbing (also exercised by the CPU tests with gloo) -------------------------
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(
+        os.environ.get("LOCAL_RANK", 0))
+
+
+def max_over_ranks(value, world, device=None):
+    """Max of a float over all ranks (identity when world == 1)."""
+    if world == 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(elems_per_rank, world, max_seconds):
+    """Units processed by all ranks divided by the slowest rank's time."""
+    return elems_per_rank * world / max_seconds
+
+
+# ---- helpers ---------------------------------------------------------------------------------
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        loaded = [v for v in sm if smax and v >= 0.5 * max(smax)] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def source_digest():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2106_00124_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel, workload):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel
+    sources are unchanged since it was taken; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            tab = json.load(f)
+        ent = tab.get(workload, {}).get(kernel)
+        if ent and ent.get("source_digest") == source_digest():
+            return float(ent["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+def pass_bytes(kernel, level, elems, dtype):
+    """Algorithmic (compulsory) bytes of one launch: every element the pass
+    must read once plus every element it must write once."""
+    if level == 0:
+        rd = BYTES[dtype] if kernel in ("segment_reduce",) else OUT_BYTES[dtype]
+        wr = OUT_BYTES[dtype]
+    else:
+        car = 8 if dtype in ("f32", "bf16") else BYTES[dtype]
+        rd = wr = car
+    if kernel == "bdbs_along_dim":
+        return elems * (rd + wr)
+    if kernel == "dim1_prefix_suffix_contrib":
+        return elems * (rd + wr)
+    if kernel == "segment_reduce":
+        return elems * rd
+    return elems * rd
+
+
+# ---- our arm -----------------------------------------------------------------------------------
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_2106_00124_gb300 as ex
+    from paper_2106_00124_gb300 import synth
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev_index = torch.cuda.current_device()
+    device = torch.device("cuda", dev_index)
+
+    dev, vals, spec = synth.workload_input(args.workload)
+    shape, k, dtype, op = spec["shape"], spec["k"], spec["dtype"], spec["op"]
+    N = int(np.prod(shape))
+    d = len(shape)
+    code, opc = ex.DTYPES[dtype], ex.OPS[op]
+    x = (torch.from_numpy(np.ascontiguousarray(dev).view(np.int16)).view(torch.bfloat16)
+         if dtype == "bf16" else torch.from_numpy(np.ascontiguousarray(dev))).to(device)
+    out_t = {"i32": torch.int32, "i64": torch.int64}.get(dtype, torch.float32)
+    out = torch.empty(shape, dtype=out_t, device=device)
+    wsb, st = ex.exsum_workspace_bytes(d, shape, k, opc, code, 1)
+    assert st == 0
+    ws = torch.empty(max(wsb, 256), dtype=torch.uint8, device=device)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=device)
+    stream = torch.cuda.current_stream(device)
+    sp = stream.cuda_stream
+
+    def step():
+        rc = ex.exsum_excluded_ws(x.data_ptr(), out.data_ptr(), d, shape, k, opc, code,
+                                  ws.data_ptr(), wsb, sp)
+        if rc != 0:
+            raise ex.ExsumError(rc, "exsum_excluded_ws")
+
+    for _ in range(args.warmup):
+        flush.fill_(1)
+        step()
+    torch.cuda.synchronize()
+
+    # ---- timed region -----------------------------------------------------------------------
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    clocks = ClockSampler(dev_index)
+    clocks.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    launches0 = ex.exsum_launch_count()
+    ex.exsum_trace_enable(True)
+    for i in range(args.steps):
+        flush.fill_(1)
+        evs[i][0].record(stream)
+        step()
+        evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    ex.exsum_trace_enable(False)
+    launches = ex.exsum_launch_count() - launches0
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    trace = ex.exsum_trace_collect(cap=max(4096, 64 * args.steps))
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    total_s = sum(step_ms) / 1e3
+    max_s = max_over_ranks(total_s, world, device)
+    value = whole_job_rate(N, world, max_s / args.steps) / 1e9
+    ms_per_step = max_s * 1e3 / args.steps
+
+    # ---- per-kernel roofline from the trace ---------------------------------------------------
+    peak, peak_kind = measured_peaks()
+    groups = {}
+    for name, level, elems, ms in trace:
+        g = groups.setdefault((name, level, elems), [0, 0.0])
+        g[0] += 1
+        g[1] += ms
+    passes = []
+    for (name, level, elems), (cnt, tot) in groups.items():
+        mean_ms = tot / cnt
+        b = pass_bytes(name, level, elems, dtype)
+        passes.append({"kernel": name, "level": level, "elems": elems, "launches": cnt,
+                       "mean_us": round(mean_ms * 1e3, 3), "share": 0.0,
+                       "algo_bytes": b, "achieved_gbs": round(b / (mean_ms * 1e-3) / 1e9, 1)})
+    total_kernel_ms = sum(p["mean_us"] * p["launches"] for p in passes) or 1.0
+    for p_ in passes:
+        p_["share"] = round(p_["mean_us"] * p_["launches"] / total_kernel_ms, 4)
+    passes.sort(key=lambda p_: -p_["share"])
+    dom = passes[0] if passes else None
+    roofline = None
+    if dom:
+        achieved = dom["achieved_gbs"]
+        roofline = {"bound": "hbm", "kernel": dom["kernel"], "level": dom["level"],
+                    "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                    "frac": round(achieved / peak, 4),
+                    "traffic": profiled_traffic(dom["kernel"], args.workload),
+                    "algo_bytes_per_launch": dom["algo_bytes"]}
+    one_rw = N * (BYTES[dtype] + OUT_BYTES[dtype])
+
+    # ---- end to end through the public API with host buffers ----------------------------------
+    e2e = None
+    if not args.no_e2e:
+        host_in = torch.empty(x.shape, dtype=x.dtype, pin_memory=True)
+        host_in.copy_(x.cpu())
+        host_out = torch.empty(out.shape, dtype=out.dtype, pin_memory=True)
+        xin = torch.empty_like(x)
+        e2e_steps = max(3, min(args.steps, 200))
+
+        def e2e_step():
+            xin.copy_(host_in, non_blocking=True)
+            rc = ex.exsum_excluded_ws(xin.data_ptr(), out.data_ptr(), d, shape, k, opc, code,
+                                      ws.data_ptr(), wsb, sp)
+            if rc != 0:
+                raise ex.ExsumError(rc, "exsum_excluded_ws")
+            host_out.copy_(out, non_blocking=True)
+
+        for _ in range(3):
+            e2e_step()
+        torch.cuda.synchronize()
+        e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                for _ in range(e2e_steps)]
+        for i in range(e2e_steps):
+            flush.fill_(1)
+            e_ev[i][0].record(stream)
+            e2e_step()
+            e_ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        e_s = sum(a.elapsed_time(b) for a, b in e_ev) / 1e3 / e2e_steps
+        e_s = max_over_ranks(e_s, world, device)
+        e2e = {"value": round(whole_job_rate(N, world, e_s) / 1e9, 3), "unit": UNIT,
+               "h2d_bytes_per_step": x.numel() * x.element_size(),
+               "d2h_bytes_per_step": out.numel() * out.element_size(), "steps": e2e_steps}
+
+    # ---- CPU oracle baseline (rank 0, N = 1 only) ------------------------------------------------
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(vals, spec, budget_s=12.0)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
+            "data": "synthetic (seeded Philox, uniform; shapes of the paper's workloads)",
+            "config": {"workload": args.workload, "shape": list(shape), "k": list(k), "op": op,
+                       "l2": "flushed between steps (256 MiB write outside the timed spans)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "roofline": roofline,
+            "one_read_one_write": {"bytes": one_rw, "achieved_gbs":
+                                   round(one_rw / (ms_per_step * 1e-3) / 1e9, 1),
+                                   "frac": round(one_rw / (ms_per_step * 1e-3) / 1e9 / peak, 4)},
+            "passes": passes,
+            "e2e": e2e, "gpu_launches": launches, "clocks": clk, "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def cpu_baseline(vals, spec, budget_s):
+    """The CPU oracle's box-complement timed on this host, on whole tensors
+    of the workload when one run fits the budget, else on leading slabs."""
+    import numpy as np
+    from oracle import oracle
+    shape, k, op = spec["shape"], spec["k"], spec["op"]
+    sample = np.ascontiguousarray(vals[:1]) if len(shape) > 1 else np.ascontiguousarray(
+        vals[: 1 << 16])
+    t0 = time.perf_counter()
+    oracle.box_complement(sample, [min(kk, nn) for kk, nn in zip(k, sample.shape)], op)
+    per_elem = (time.perf_counter() - t0) / sample.size
+    N = int(np.prod(shape))
+    if per_elem * N <= budget_s:
+        runs = max(1, int(budget_s // (per_elem * N)))
+        t0 = time.perf_counter()
+        for _ in range(runs):
+            oracle.box_complement(vals, k, op)
+        dt = time.perf_counter() - t0
+        return {"value": round(runs * N / dt / 1e9, 5), "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": "%d run(s) of the whole %s tensor, single-threaded C oracle "
+                          "(box-complement)" % (runs, "x".join(map(str, shape)))}
+    rows = max(1, int(budget_s / (per_elem * (N // shape[0]))))
+    rows = min(rows, shape[0])
+    slab = np.ascontiguousarray(vals[:rows])
+    kk = [min(a, b) for a, b in zip(k, slab.shape)]
+    t0 = time.perf_counter()
+    oracle.box_complement(slab, kk, op)
+    dt = time.perf_counter() - t0
+    return {"value": round(slab.size / dt / 1e9, 5), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "leading %d of %d slabs along dim 1, single-threaded C oracle" % (
+                rows, shape[0])}
+
+
+# ---- reference arm: the CPU oracle -------------------------------------------------------------
+
+def run_reference(args):
+    import numpy as np
+    from oracle import oracle
+    from paper_2106_00124_gb300 import synth
+
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    oracle.build()
+    dev, vals, spec = synth.workload_input(args.workload)
+    shape, k, op = spec["shape"], spec["k"], spec["op"]
+    # Each step runs the oracle on the leading slab of the tensor along dim 1,
+    # sized so the whole run stays near two minutes of CPU time.
+    probe = np.ascontiguousarray(vals[:1]) if len(shape) > 1 else np.ascontiguousarray(vals[:4096])
+    t0 = time.perf_counter()
+    oracle.box_complement(probe, [min(a, b) for a, b in zip(k, probe.shape)], op)
+    per_elem = (time.perf_counter() - t0) / probe.size
+    budget_per_step = 120.0 / max(1, args.steps + args.warmup)
+    if len(shape) > 1:
+        plane = int(np.prod(shape[1:]))
+        rows = int(max(1, min(shape[0], budget_per_step / (per_elem * plane))))
+        sample = np.ascontiguousarray(vals[:rows])
+        desc = "leading %d of %d slabs along dim 1 per step" % (rows, shape[0])
+    else:
+        n = int(max(k[0], min(shape[0], budget_per_step / per_elem)))
+        sample = np.ascontiguousarray(vals[:n])
+        desc = "leading %d of %d elements per step" % (n, shape[0])
+    kk = [min(a, b) for a, b in zip(k, sample.shape)]
+    for _ in range(args.warmup):
+        oracle.box_complement(sample, kk, op)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.box_complement(sample, kk, op)
+    dt = time.perf_counter() - t0
+    value = sample.size * args.steps / dt / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(dt * 1e3 / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": spec["dtype"], "data": "synthetic",
+        "config": {"workload": args.workload, "shape": list(shape), "k": list(k), "op": op},
+        "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

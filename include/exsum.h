@@ -132,6 +132,27 @@ int exsum_excluded_ws(const void *in, void *out, int d, const int64_t *shape, co
  * device first).  Returns 0 or EXSUM_ECUDA. */
 int exsum_release_cached_workspace(void);
 
+/*
+ * Launch trace.  The paper reports time per element (Sec. 6); this breaks a
+ * call's device time down by pass.  While enabled, every kernel the library
+ * launches is bracketed by a pair of CUDA events recorded on the stream it
+ * is launched on.  exsum_trace_collect waits for the recorded events, writes
+ * up to `cap` records in launch order -- kernel tag (see exsum_kernel_name),
+ * recursion level of box-complement (0 = the input tensor), elements the
+ * pass covers, device milliseconds -- clears the trace and returns the
+ * number of records made (which may exceed cap), or EXSUM_ECUDA.  Any of
+ * the output arrays may be NULL.  Tracing during stream capture is not
+ * supported.
+ */
+void exsum_trace_enable(int on);
+int exsum_trace_collect(int *tags, int *levels, int64_t *elems, float *ms, int cap);
+
+/* Static name of a kernel tag ("unknown" for others). */
+const char *exsum_kernel_name(int tag);
+
+/* Kernels launched by the library in this process so far. */
+int64_t exsum_launch_count(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -62,6 +62,12 @@ _SIG = {
     "exsum_excluded_ws": ([_P, _P, ctypes.c_int, _I64P, _I64P, ctypes.c_int, ctypes.c_int, _P,
                            ctypes.c_size_t, _P], ctypes.c_int),
     "exsum_release_cached_workspace": ([], ctypes.c_int),
+    "exsum_trace_enable": ([ctypes.c_int], None),
+    "exsum_trace_collect": ([ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                             ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_float),
+                             ctypes.c_int], ctypes.c_int),
+    "exsum_kernel_name": ([ctypes.c_int], ctypes.c_char_p),
+    "exsum_launch_count": ([], ctypes.c_int64),
 }
 
 
@@ -145,6 +151,30 @@ def exsum_excluded_ws(in_ptr, out_ptr, d, shape, k, op, dtype, ws_ptr, ws_bytes,
 
 def exsum_release_cached_workspace():
     return _load().exsum_release_cached_workspace()
+
+
+def exsum_trace_enable(on):
+    _load().exsum_trace_enable(int(bool(on)))
+
+
+def exsum_trace_collect(cap=4096):
+    """Returns a list of (kernel_name, level, elements, ms) and clears the trace."""
+    tags = (ctypes.c_int * cap)()
+    levels = (ctypes.c_int * cap)()
+    elems = (ctypes.c_int64 * cap)()
+    ms = (ctypes.c_float * cap)()
+    n = _load().exsum_trace_collect(tags, levels, elems, ms, cap)
+    if n < 0:
+        raise ExsumError(n, "exsum_trace_collect")
+    return [(exsum_kernel_name(tags[i]), levels[i], elems[i], ms[i]) for i in range(min(n, cap))]
+
+
+def exsum_kernel_name(tag):
+    return _load().exsum_kernel_name(int(tag)).decode()
+
+
+def exsum_launch_count():
+    return int(_load().exsum_launch_count())
 
 
 # ---- torch conveniences ------------------------------------------------------------------------

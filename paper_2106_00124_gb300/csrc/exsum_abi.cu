@@ -2,9 +2,11 @@
 // dtype/operator dispatch, and the per-(device, stream) workspace cache.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <utility>
+#include <vector>
 
 #include "../../include/exsum.h"
 #include "pipeline.cuh"
@@ -21,6 +23,59 @@ int dispatch_bf16(int, int, const void *, void *, int, const int64_t *, const in
 }  // namespace exsum
 
 static thread_local int g_last_cuda_error = 0;
+
+// ---- launch trace and launch counter --------------------------------------------------------
+namespace {
+struct TraceRec {
+    int tag, level;
+    int64_t elems;
+    cudaEvent_t ev0, ev1;
+};
+std::atomic<int64_t> g_launches{0};
+std::atomic<int> g_trace_on{0};
+std::mutex g_trace_mu;
+std::vector<TraceRec> g_trace;
+std::vector<cudaEvent_t> g_event_pool;
+thread_local int g_pending = -1;
+
+cudaEvent_t pool_event()
+{
+    if (!g_event_pool.empty()) {
+        cudaEvent_t e = g_event_pool.back();
+        g_event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+}  // namespace
+
+namespace exsum {
+void trace_before(cudaStream_t s, int tag, int level, int64_t elems)
+{
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    g_pending = -1;
+    if (!g_trace_on.load(std::memory_order_relaxed)) return;
+    std::lock_guard<std::mutex> lock(g_trace_mu);
+    TraceRec r{tag, level, elems, pool_event(), pool_event()};
+    if (!r.ev0 || !r.ev1) return;
+    cudaEventRecord(r.ev0, s);
+    g_trace.push_back(r);
+    g_pending = (int)g_trace.size() - 1;
+}
+
+void trace_after(cudaStream_t s)
+{
+    if (g_pending < 0) return;
+    std::lock_guard<std::mutex> lock(g_trace_mu);
+    if (g_pending < (int)g_trace.size()) cudaEventRecord(g_trace[g_pending].ev1, s);
+    g_pending = -1;
+}
+}  // namespace exsum
 
 static int validate(int d, const int64_t *shape, const int64_t *k, int op, int dtype)
 {
@@ -202,6 +257,50 @@ int exsum_excluded_ws(const void *in, void *out, int d, const int64_t *shape, co
     if (!in || !out) return EXSUM_EINVAL;
     return run(1, in, out, d, shape, k, op, dtype, workspace, workspace_bytes, stream, nullptr);
 }
+
+void exsum_trace_enable(int on) { g_trace_on.store(on ? 1 : 0); }
+
+int exsum_trace_collect(int *tags, int *levels, int64_t *elems, float *ms, int cap)
+{
+    std::lock_guard<std::mutex> lock(g_trace_mu);
+    int n = 0;
+    int rc = 0;
+    for (auto &r : g_trace) {
+        float t = -1.f;
+        cudaError_t e = cudaEventSynchronize(r.ev1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, r.ev0, r.ev1);
+        if (e != cudaSuccess) {
+            g_last_cuda_error = (int)e;
+            cudaGetLastError();
+            rc = EXSUM_ECUDA;
+        }
+        if (n < cap) {
+            if (tags) tags[n] = r.tag;
+            if (levels) levels[n] = r.level;
+            if (elems) elems[n] = r.elems;
+            if (ms) ms[n] = t;
+        }
+        ++n;
+        g_event_pool.push_back(r.ev0);
+        g_event_pool.push_back(r.ev1);
+    }
+    g_trace.clear();
+    return rc ? rc : n;
+}
+
+const char *exsum_kernel_name(int tag)
+{
+    switch (tag) {
+    case exsum::TAG_INC: return "bdbs_along_dim";
+    case exsum::TAG_REDUCE: return "segment_reduce";
+    case exsum::TAG_SUMSEG: return "segment_totals";
+    case exsum::TAG_CARRY: return "dim1_carries";
+    case exsum::TAG_EXLINE: return "dim1_prefix_suffix_contrib";
+    default: return "unknown";
+    }
+}
+
+int64_t exsum_launch_count(void) { return g_launches.load(); }
 
 int exsum_release_cached_workspace(void)
 {

@@ -18,6 +18,20 @@ namespace exsum {
 // Status codes, mirrored from include/exsum.h (kept numerically identical).
 enum { ST_OK = 0, ST_EINVAL = -1, ST_ENOMEM = -2, ST_EUNSUP = -3, ST_ECUDA = -4 };
 
+// Kernel tags reported by the launch trace (exsum_trace_*).
+enum KernelTag {
+    TAG_INC = 0,       // BDBS-Along-Dim line pass
+    TAG_REDUCE = 1,    // segment / column reductions
+    TAG_SUMSEG = 2,    // segment totals -> column totals
+    TAG_CARRY = 3,     // dimension-1 carries
+    TAG_EXLINE = 4,    // dimension-1 prefix/suffix + contributions
+    TAG_COUNT = 5
+};
+
+// Launch bracketing for the trace and the launch counter (exsum_abi.cu).
+void trace_before(cudaStream_t s, int tag, int level, int64_t elems);
+void trace_after(cudaStream_t s);
+
 struct Ctx {
     char *base = nullptr;   // workspace (device)
     size_t cap = 0;         // workspace bytes available
@@ -26,6 +40,7 @@ struct Ctx {
     cudaStream_t stream = 0;
     int status = ST_OK;
     cudaError_t cuda_err = cudaSuccess;
+    int level = 0;           // recursion depth of box-complement (0 = input tensor)
 
     template <class T>
     T *take(int64_t count)
@@ -37,9 +52,11 @@ struct Ctx {
         return p;
     }
     bool ok() const { return status == ST_OK; }
+    void before(int tag, int64_t elems) { trace_before(stream, tag, level, elems); }
     void check_launch()
     {
         if (dry) return;
+        trace_after(stream);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess && status == ST_OK) {
             status = ST_ECUDA;
@@ -81,6 +98,7 @@ struct Pipe {
         auto kern = k_inc_lines<M, SIn, SOut>;
         if (smem > 48 * 1024)
             cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cx.before(TAG_INC, O * n * I);
         kern<<<(unsigned)cdiv(total, threads), threads, smem, cx.stream>>>(src, dst, O, n, I, k, Lc,
                                                                            nchunks, gslots);
         cx.check_launch();
@@ -98,6 +116,7 @@ struct Pipe {
         S = cdiv(n1, L);
         if (S == 1) {
             if (cx.dry) return;
+            cx.before(TAG_REDUCE, n1 * Mc);
             k_reduce_seg<M, SIn><<<(unsigned)cdiv(Mc, 256), 256, 0, cx.stream>>>(X, G, nullptr, n1,
                                                                                   Mc, L, 1, 0);
             cx.check_launch();
@@ -105,9 +124,11 @@ struct Pipe {
         }
         CAR *Rx = cx.take<CAR>(S * Mc);
         if (cx.dry || !cx.ok()) return;
+        cx.before(TAG_REDUCE, n1 * Mc);
         k_reduce_seg<M, SIn><<<(unsigned)cdiv(S * Mc, 256), 256, 0, cx.stream>>>(X, Rx, nullptr, n1,
                                                                                   Mc, L, S, 0);
         cx.check_launch();
+        cx.before(TAG_SUMSEG, S * Mc);
         if (Mc >= 1024)
             k_sum_segs_col<M><<<(unsigned)cdiv(Mc, 256), 256, 0, cx.stream>>>(Rx, G, Mc, S);
         else
@@ -131,10 +152,12 @@ struct Pipe {
             const bool blk = S > 64 && Mc < 4096;
             CAR *SR = blk ? cx.take<CAR>(S * Mc) : nullptr;
             if (cx.dry || !cx.ok()) return;
+            cx.before(TAG_REDUCE, n1 * Mc);
             k_reduce_seg<M, SH><<<(unsigned)cdiv(S * Mc, 256), 256, 0, cx.stream>>>(
                 H, R, Rt, n1, Mc, EXL, S, k1 % EXL);
             cx.check_launch();
             const int64_t qoff = 1 + k1 / EXL;
+            cx.before(TAG_CARRY, S * Mc);
             if (blk)
                 k_carry_blk<M, 1024><<<(unsigned)Mc, 1024, 0, cx.stream>>>(R, Rt, T, Qb, SR, Mc, S,
                                                                            qoff);
@@ -146,6 +169,7 @@ struct Pipe {
             qs = Mc;
         }
         if (cx.dry || !cx.ok()) return;
+        cx.before(TAG_EXLINE, n1 * Mc);
         k_exline<M, SH, SOut, EXL><<<(unsigned)cdiv(S * Mc, 128), 128, 0, cx.stream>>>(
             H, Q, qs, out, n1, Mc, k1, S);
         cx.check_launch();
@@ -223,7 +247,9 @@ struct Pipe {
             cur = dst;
         }
         colsum<SIn>(cx, X, G, n[0], M1);
+        cx.level++;
         excluded<CAR, CAR>(cx, G, T, d - 1, n + 1, k + 1);
+        cx.level--;
         if (P > 0)
             exline_stage<SOut, SOut>(cx, B, T, out, n[0], M1, k[0]);
         else
