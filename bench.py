@@ -9,10 +9,13 @@ line (rank 0).
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
   python bench.py --impl reference ...   # the CPU oracle, timed on host cores
 
-Timing: each step is bracketed by CUDA events on the stream the library
-launches on; between steps a 256 MiB buffer is written to flush the 129 MB
-L2, outside the timed spans.  `value` sums the K step spans; the per-kernel
-roofline comes from the library's launch trace over the same timed region.
+Timing: the step is captured once into a CUDA graph; each replay is
+bracketed by CUDA events on the stream it runs on, and between steps a
+256 MiB buffer is written to flush the 129 MB L2, outside the timed spans.
+`value` sums the K step spans; the per-kernel roofline comes from the
+library's launch trace (event-record nodes around every kernel node of the
+graph) read after each replay of the same timed region.  `e2e` calls the C
+ABI directly (no graph) with host input and output buffers.
 """
 
 import argparse
@@ -215,15 +218,31 @@ def run_ours(args):
     stream = torch.cuda.current_stream(device)
     sp = stream.cuda_stream
 
-    def step():
+    def step(stream_ptr):
         rc = ex.exsum_excluded_ws(x.data_ptr(), out.data_ptr(), d, shape, k, opc, code,
-                                  ws.data_ptr(), wsb, sp)
+                                  ws.data_ptr(), wsb, stream_ptr)
         if rc != 0:
             raise ex.ExsumError(rc, "exsum_excluded_ws")
 
+    for _ in range(max(1, min(args.warmup, 3))):
+        flush.fill_(1)
+        step(sp)
+    torch.cuda.synchronize()
+
+    # The step is captured once into a CUDA graph (all of its launches), with
+    # the launch trace on: each kernel node is bracketed by event-record nodes
+    # whose times are read back after every replay.
+    ex.exsum_trace_collect(clear=True)
+    graph = torch.cuda.CUDAGraph()
+    launches0 = ex.exsum_launch_count()
+    ex.exsum_trace_enable(True)
+    with torch.cuda.graph(graph):
+        step(torch.cuda.current_stream().cuda_stream)
+    ex.exsum_trace_enable(False)
+    launches_per_step = ex.exsum_launch_count() - launches0
     for _ in range(args.warmup):
         flush.fill_(1)
-        step()
+        graph.replay()
     torch.cuda.synchronize()
 
     # ---- timed region -----------------------------------------------------------------------
@@ -234,20 +253,20 @@ def run_ours(args):
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    launches0 = ex.exsum_launch_count()
-    ex.exsum_trace_enable(True)
+    trace = []
     for i in range(args.steps):
         flush.fill_(1)
         evs[i][0].record(stream)
-        step()
+        graph.replay()
         evs[i][1].record(stream)
+        torch.cuda.synchronize()
+        trace.extend(ex.exsum_trace_collect(cap=256, clear=False))
     torch.cuda.synchronize()
-    ex.exsum_trace_enable(False)
-    launches = ex.exsum_launch_count() - launches0
+    launches = launches_per_step * args.steps
     if world > 1:
         torch.distributed.barrier()
     clk = clocks.stop()
-    trace = ex.exsum_trace_collect(cap=max(4096, 64 * args.steps))
+    ex.exsum_trace_collect(clear=True)
     step_ms = [a.elapsed_time(b) for a, b in evs]
     total_s = sum(step_ms) / 1e3
     max_s = max_over_ranks(total_s, world, device)
@@ -295,7 +314,7 @@ def run_ours(args):
         def e2e_step():
             xin.copy_(host_in, non_blocking=True)
             rc = ex.exsum_excluded_ws(xin.data_ptr(), out.data_ptr(), d, shape, k, opc, code,
-                                      ws.data_ptr(), wsb, sp)
+                                      ws.data_ptr(), wsb, sp)  # plain launches, no graph
             if rc != 0:
                 raise ex.ExsumError(rc, "exsum_excluded_ws")
             host_out.copy_(out, non_blocking=True)

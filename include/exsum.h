@@ -136,16 +136,18 @@ int exsum_release_cached_workspace(void);
  * Launch trace.  The paper reports time per element (Sec. 6); this breaks a
  * call's device time down by pass.  While enabled, every kernel the library
  * launches is bracketed by a pair of CUDA events recorded on the stream it
- * is launched on.  exsum_trace_collect waits for the recorded events, writes
- * up to `cap` records in launch order -- kernel tag (see exsum_kernel_name),
- * recursion level of box-complement (0 = the input tensor), elements the
- * pass covers, device milliseconds -- clears the trace and returns the
- * number of records made (which may exceed cap), or EXSUM_ECUDA.  Any of
- * the output arrays may be NULL.  Tracing during stream capture is not
- * supported.
+ * is launched on (inside a stream capture the pair becomes two event-record
+ * nodes of the graph, re-recorded on every replay).  exsum_trace_collect
+ * waits for the recorded events, writes up to `cap` records in launch order
+ * -- kernel tag (see exsum_kernel_name), recursion level of box-complement
+ * (0 = the input tensor), elements the pass covers, device milliseconds --
+ * and returns the number of records (which may exceed cap), or EXSUM_ECUDA.
+ * With clear != 0 the trace is emptied; with clear == 0 it is kept, so the
+ * records of a captured graph can be read again after each replay.  Any of
+ * the output arrays may be NULL.
  */
 void exsum_trace_enable(int on);
-int exsum_trace_collect(int *tags, int *levels, int64_t *elems, float *ms, int cap);
+int exsum_trace_collect(int *tags, int *levels, int64_t *elems, float *ms, int cap, int clear);
 
 /* Static name of a kernel tag ("unknown" for others). */
 const char *exsum_kernel_name(int tag);

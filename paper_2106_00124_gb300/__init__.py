@@ -65,7 +65,7 @@ _SIG = {
     "exsum_trace_enable": ([ctypes.c_int], None),
     "exsum_trace_collect": ([ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                              ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_float),
-                             ctypes.c_int], ctypes.c_int),
+                             ctypes.c_int, ctypes.c_int], ctypes.c_int),
     "exsum_kernel_name": ([ctypes.c_int], ctypes.c_char_p),
     "exsum_launch_count": ([], ctypes.c_int64),
 }
@@ -157,13 +157,13 @@ def exsum_trace_enable(on):
     _load().exsum_trace_enable(int(bool(on)))
 
 
-def exsum_trace_collect(cap=4096):
-    """Returns a list of (kernel_name, level, elements, ms) and clears the trace."""
+def exsum_trace_collect(cap=4096, clear=True):
+    """Returns a list of (kernel_name, level, elements, ms); clears the trace if asked."""
     tags = (ctypes.c_int * cap)()
     levels = (ctypes.c_int * cap)()
     elems = (ctypes.c_int64 * cap)()
     ms = (ctypes.c_float * cap)()
-    n = _load().exsum_trace_collect(tags, levels, elems, ms, cap)
+    n = _load().exsum_trace_collect(tags, levels, elems, ms, cap, int(bool(clear)))
     if n < 0:
         raise ExsumError(n, "exsum_trace_collect")
     return [(exsum_kernel_name(tags[i]), levels[i], elems[i], ms[i]) for i in range(min(n, cap))]

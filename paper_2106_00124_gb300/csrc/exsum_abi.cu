@@ -38,6 +38,17 @@ std::vector<TraceRec> g_trace;
 std::vector<cudaEvent_t> g_event_pool;
 thread_local int g_pending = -1;
 
+// Records ev on s; inside a stream capture the record becomes an event-record
+// node of the graph (re-recorded on every replay).
+void record_event(cudaEvent_t ev, cudaStream_t s)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+        cudaEventRecordWithFlags(ev, s, cudaEventRecordExternal);
+    else
+        cudaEventRecord(ev, s);
+}
+
 cudaEvent_t pool_event()
 {
     if (!g_event_pool.empty()) {
@@ -63,7 +74,7 @@ void trace_before(cudaStream_t s, int tag, int level, int64_t elems)
     std::lock_guard<std::mutex> lock(g_trace_mu);
     TraceRec r{tag, level, elems, pool_event(), pool_event()};
     if (!r.ev0 || !r.ev1) return;
-    cudaEventRecord(r.ev0, s);
+    record_event(r.ev0, s);
     g_trace.push_back(r);
     g_pending = (int)g_trace.size() - 1;
 }
@@ -72,7 +83,7 @@ void trace_after(cudaStream_t s)
 {
     if (g_pending < 0) return;
     std::lock_guard<std::mutex> lock(g_trace_mu);
-    if (g_pending < (int)g_trace.size()) cudaEventRecord(g_trace[g_pending].ev1, s);
+    if (g_pending < (int)g_trace.size()) record_event(g_trace[g_pending].ev1, s);
     g_pending = -1;
 }
 }  // namespace exsum
@@ -260,7 +271,7 @@ int exsum_excluded_ws(const void *in, void *out, int d, const int64_t *shape, co
 
 void exsum_trace_enable(int on) { g_trace_on.store(on ? 1 : 0); }
 
-int exsum_trace_collect(int *tags, int *levels, int64_t *elems, float *ms, int cap)
+int exsum_trace_collect(int *tags, int *levels, int64_t *elems, float *ms, int cap, int clear)
 {
     std::lock_guard<std::mutex> lock(g_trace_mu);
     int n = 0;
@@ -281,10 +292,12 @@ int exsum_trace_collect(int *tags, int *levels, int64_t *elems, float *ms, int c
             if (ms) ms[n] = t;
         }
         ++n;
-        g_event_pool.push_back(r.ev0);
-        g_event_pool.push_back(r.ev1);
+        if (clear) {
+            g_event_pool.push_back(r.ev0);
+            g_event_pool.push_back(r.ev1);
+        }
     }
-    g_trace.clear();
+    if (clear) g_trace.clear();
     return rc ? rc : n;
 }
 

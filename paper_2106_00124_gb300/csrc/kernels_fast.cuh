@@ -1,0 +1,299 @@
+// kernels_fast.cuh -- register-resident kernels for the common box sizes.
+//
+// BDBS-1D (Sec. 3) needs, for the block of k elements holding x, the suffix
+// of that block from x and the prefix of the next block up to x+k-1.  Here a
+// thread keeps both blocks in registers: arrays of compile-time length KMAX
+// hold a block of runtime length k <= KMAX, padded with the identity e, so
+// every register index is a compile-time constant (no local memory) and the
+// padding contributes nothing (Sec. 3 footnote: padding with e).  One thread
+// walks one line chunk; per element it performs one prefix step, one suffix
+// step and one combine (Combine-Along-Row).
+#pragma once
+
+#include "kernels_lines.cuh"
+
+namespace exsum {
+
+// Walks outputs [r0, rend) of one line.  ld(x) returns the element at line
+// position x as loc_t (e beyond the data); st(x, v) stores output x.
+template <class M, int KMAX, class LD, class ST>
+__device__ __forceinline__ void bdbs_walk(int k, int r0, int rend, LD ld, ST st)
+{
+    using Lt = typename M::loc_t;
+    Lt S[KMAX], v[KMAX];
+#pragma unroll
+    for (int j = 0; j < KMAX; ++j) v[j] = (j < k) ? ld(r0 + j) : M::lid();
+    S[KMAX - 1] = v[KMAX - 1];
+#pragma unroll
+    for (int j = KMAX - 2; j >= 0; --j) S[j] = M::lop(v[j], S[j + 1]);
+    for (int sb = r0; sb < rend; sb += k) {
+        st(sb, S[0]);
+        const int nb = sb + k;
+#pragma unroll
+        for (int j = 0; j < KMAX; ++j) v[j] = (j < k) ? ld(nb + j) : M::lid();
+        Lt p = M::lid();
+#pragma unroll
+        for (int j = 0; j + 1 < KMAX; ++j) {
+            p = M::lop(p, v[j]);
+            if (j + 1 < k && sb + 1 + j < rend) st(sb + 1 + j, M::lop(S[j + 1], p));
+        }
+        S[KMAX - 1] = v[KMAX - 1];
+#pragma unroll
+        for (int j = KMAX - 2; j >= 0; --j) S[j] = M::lop(v[j], S[j + 1]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// BDBS-Along-Dim along a strided dimension (view [O, n, I], I > 1): one
+// thread per (outer, chunk, inner) line chunk; consecutive threads take
+// consecutive inner positions, so every load and store is coalesced.
+// ---------------------------------------------------------------------------
+template <class M, class SIn, class SOut, int KMAX>
+__global__ void __launch_bounds__(128)
+k_inc_strided(const SIn *__restrict__ in, SOut *__restrict__ out, int64_t O, int n, int64_t I,
+              int k, int Lc, int nchunks)
+{
+    const int64_t total = O * nchunks * I;
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= total) return;
+    const int64_t i = gid % I;
+    const int64_t rest = gid / I;
+    const int ch = (int)(rest % nchunks);
+    const int64_t o = rest / nchunks;
+    const SIn *src = in + o * n * I + i;
+    SOut *dst = out + o * n * I + i;
+    const int r0 = ch * Lc;
+    const int rend = min(r0 + Lc, n);
+    bdbs_walk<M, KMAX>(
+        k, r0, rend,
+        [&](int x) { return x < n ? M::lget(src[(int64_t)x * I]) : M::lid(); },
+        [&](int x, typename M::loc_t v) { dst[(int64_t)x * I] = M::template lput<SOut>(v); });
+}
+
+// ---------------------------------------------------------------------------
+// BDBS-Along-Dim along the contiguous dimension (rows of length n).  A block
+// takes ROWS "virtual rows" (row, chunk of Lc outputs), stages each with its
+// k-1 halo into a padded shared-memory tile with coalesced loads, lets one
+// thread walk each virtual row from shared memory (odd row stride: the
+// threads of a warp hit distinct banks), writes results back in place and
+// stores them coalesced.
+// ---------------------------------------------------------------------------
+template <class M, class SIn, class SOut, int KMAX, int ROWS>
+__global__ void __launch_bounds__(ROWS)
+k_inc_contig(const SIn *__restrict__ in, SOut *__restrict__ out, int64_t nrows, int n, int k,
+             int Lc, int nchunks, int W, uint32_t wl_magic, int WL)
+{
+    using Lt = typename M::loc_t;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Lt *tile = reinterpret_cast<Lt *>(smem_raw);
+    __shared__ int64_t row_off[ROWS];   // global offset of position p0 of each tile row
+    __shared__ int row_lim[ROWS];       // positions of the tile row that exist (n - p0)
+    const int64_t v0 = (int64_t)blockIdx.x * ROWS;        // first virtual row
+    const int64_t nvirt = nrows * nchunks;
+    const int tid = threadIdx.x;
+    {
+        const int64_t vr = v0 + tid;
+        int64_t off = 0;
+        int lim = 0;
+        if (vr < nvirt) {
+            const int64_t row = vr / nchunks;
+            const int p0 = (int)(vr - row * nchunks) * Lc;
+            off = row * n + p0;
+            lim = n - p0;
+        }
+        row_off[tid] = off;
+        row_lim[tid] = lim;
+    }
+    __syncthreads();
+    // Stage: tile row r holds positions p0 .. p0+WL-1 of its row (e past n).
+    for (int e = tid; e < ROWS * WL; e += ROWS) {
+        const int r = (int)__umulhi((uint32_t)e, wl_magic);
+        const int x = e - r * WL;
+        tile[r * W + x] = x < row_lim[r] ? M::lget(in[row_off[r] + x]) : M::lid();
+    }
+    __syncthreads();
+    {
+        const int len = min(Lc, row_lim[tid]);
+        Lt *trow = tile + tid * W;
+        bdbs_walk<M, KMAX>(
+            k, 0, len, [&](int x) { return x < WL ? trow[x] : M::lid(); },
+            [&](int x, Lt v) { trow[x] = v; });
+    }
+    __syncthreads();
+    for (int e = tid; e < ROWS * WL; e += ROWS) {
+        const int r = (int)__umulhi((uint32_t)e, wl_magic);
+        const int x = e - r * WL;
+        if (x < Lc && x < row_lim[r]) out[row_off[r] + x] = M::template lput<SOut>(tile[r * W + x]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Rows [ya, yb) of column c of a view [*, Mc], reduced with short fp32 runs
+// (at most 32 rows) combined into the long accumulator.
+// ---------------------------------------------------------------------------
+template <class M, class SIn>
+__device__ __forceinline__ typename M::acc_t reduce_rows(const SIn *__restrict__ col, int64_t Mc,
+                                                         int64_t ya, int64_t yb)
+{
+    typename M::acc_t acc = M::id();
+    for (int64_t y0 = ya; y0 < yb; y0 += 32) {
+        const int64_t y1 = min(y0 + 32, yb);
+        typename M::loc_t l = M::lid();
+#pragma unroll 8
+        for (int64_t y = y0; y < y1; ++y) l = M::lop(l, M::lget(col[y * Mc]));
+        acc = M::op(acc, M::widen(l));
+    }
+    return acc;
+}
+
+// Segment reductions along dimension 1 of a view [n1, Mc]: R[s][c] over rows
+// [s*L, s*L+L) and Rt[s][c] over the same rows from offset r on.
+template <class M, class SIn>
+__global__ void __launch_bounds__(256)
+k_reduce_seg2(const SIn *__restrict__ X, typename M::car_t *__restrict__ R,
+              typename M::car_t *__restrict__ Rt, int64_t n1, int64_t Mc, int64_t L, int64_t S,
+              int64_t r)
+{
+    using C = typename M::car_t;
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= S * Mc) return;
+    const int64_t c = gid % Mc, s = gid / Mc;
+    const int64_t y0 = s * L;
+    const int64_t y1 = min(y0 + L, n1);
+    const int64_t ys = min(y0 + r, y1);
+    const SIn *col = X + c;
+    const typename M::acc_t head = reduce_rows<M>(col, Mc, y0, ys);
+    const typename M::acc_t tail = reduce_rows<M>(col, Mc, ys, y1);
+    R[gid] = M::template put<C>(M::op(head, tail));
+    if (Rt) Rt[gid] = M::template put<C>(tail);
+}
+
+// ---------------------------------------------------------------------------
+// Dimension-1 step (strided, Mc > 1): as k_exline, with the in-segment
+// prefix and suffix in the fast local accumulator and one long-accumulator
+// combine with the carry per output.
+// ---------------------------------------------------------------------------
+template <class M, class SIn, class SOut, int L>
+__global__ void __launch_bounds__(128)
+k_exline2(const SIn *__restrict__ H, const typename M::car_t *__restrict__ Q, int64_t qs,
+          SOut *__restrict__ out, int64_t n1, int64_t Mc, int64_t k1, int64_t S)
+{
+    using Lt = typename M::loc_t;
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= S * Mc) return;
+    const int64_t c = gid % Mc, s = gid / Mc;
+    const int64_t s0 = s * L;
+    const SIn *hp = H + s0 * Mc + c;
+    const SIn *tp = hp + k1 * Mc;
+    SOut *op_ = out + s0 * Mc + c;
+    Lt P[L];
+    Lt acc = M::lid();
+    const typename M::acc_t q = Q ? M::get(Q[s * qs + c]) : M::id();
+    Lt sacc = M::lid();
+    if (s0 + L + k1 <= n1) {
+#pragma unroll
+        for (int t = 0; t < L; ++t) {
+            P[t] = acc;
+            acc = M::lop(acc, M::lget(hp[t * Mc]));
+        }
+#pragma unroll
+        for (int t = L - 1; t >= 0; --t) {
+            sacc = M::lop(M::lget(tp[t * Mc]), sacc);
+            op_[t * Mc] = M::template put<SOut>(M::op(q, M::widen(M::lop(P[t], sacc))));
+        }
+    } else {
+#pragma unroll
+        for (int t = 0; t < L; ++t) {
+            P[t] = acc;
+            if (s0 + t < n1) acc = M::lop(acc, M::lget(hp[t * Mc]));
+        }
+#pragma unroll
+        for (int t = L - 1; t >= 0; --t) {
+            if (s0 + k1 + t < n1) sacc = M::lop(M::lget(tp[t * Mc]), sacc);
+            if (s0 + t < n1)
+                op_[t * Mc] = M::template put<SOut>(M::op(q, M::widen(M::lop(P[t], sacc))));
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Dimension-1 step for a single contiguous line (Mc = 1).  One block per
+// segment of NT*V outputs; thread t owns outputs s0 + t*V .. s0 + t*V + V-1.
+// It scans its V prefix-window elements and the V target-window elements
+// (positions +k1) locally, and the block scans the per-thread totals, so the
+// exclusive prefix and the target-window suffix of an output live in the
+// same thread and register slot.
+// ---------------------------------------------------------------------------
+template <class M, class SIn, class SOut, int NT, int V>
+__global__ void __launch_bounds__(NT)
+k_exline_contig(const SIn *__restrict__ H, const typename M::car_t *__restrict__ Q,
+                SOut *__restrict__ out, int64_t n1, int64_t k1)
+{
+    using Lt = typename M::loc_t;
+    using A = typename M::acc_t;
+    constexpr int L = NT * V;
+    const int64_t s = blockIdx.x;
+    const int64_t s0 = s * L + (int64_t)threadIdx.x * V;
+    Lt pre[V], suf[V];
+    Lt acc = M::lid();
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+        pre[j] = acc;
+        if (s0 + j < n1) acc = M::lop(acc, M::lget(H[s0 + j]));
+    }
+    const Lt ptot = acc;
+    Lt sacc = M::lid();
+#pragma unroll
+    for (int j = V - 1; j >= 0; --j) {
+        const int64_t y = s0 + k1 + j;
+        if (y < n1) sacc = M::lop(M::lget(H[y]), sacc);
+        suf[j] = sacc;
+    }
+    A bp, bs_unused, tp_unused, bsuf;
+    block_exscan_both<M, NT>(M::widen(ptot), bp, bs_unused);
+    block_exscan_both<M, NT>(M::widen(sacc), tp_unused, bsuf);
+    A q = Q ? M::get(Q[s]) : M::id();
+    q = M::op(q, M::op(bp, bsuf));
+#pragma unroll
+    for (int j = 0; j < V; ++j)
+        if (s0 + j < n1) out[s0 + j] = M::template put<SOut>(M::op(q, M::widen(M::lop(pre[j], suf[j]))));
+}
+
+// Segment reductions of a single contiguous line: one block per segment of
+// NT*V elements; R[s] and the tail Rt[s] from offset r.
+template <class M, class SIn, int NT, int V>
+__global__ void __launch_bounds__(NT)
+k_reduce_seg_contig(const SIn *__restrict__ X, typename M::car_t *__restrict__ R,
+                    typename M::car_t *__restrict__ Rt, int64_t n1, int64_t r)
+{
+    using Lt = typename M::loc_t;
+    using A = typename M::acc_t;
+    using C = typename M::car_t;
+    constexpr int L = NT * V;
+    const int64_t s = blockIdx.x;
+    const int64_t base = s * L;
+    const int64_t s0 = base + (int64_t)threadIdx.x * V;
+    Lt head = M::lid(), tail = M::lid();
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+        const int64_t y = s0 + j;
+        if (y < n1) {
+            const Lt v = M::lget(X[y]);
+            if (y - base < r)
+                head = M::lop(head, v);
+            else
+                tail = M::lop(tail, v);
+        }
+    }
+    A hp, hs, tpre, tsuf;
+    block_exscan_both<M, NT>(M::widen(head), hp, hs);
+    block_exscan_both<M, NT>(M::widen(tail), tpre, tsuf);
+    if (threadIdx.x == NT - 1) {
+        const A h = M::op(hp, M::widen(head));
+        const A t = M::op(tpre, M::widen(tail));
+        R[s] = M::template put<C>(M::op(h, t));
+        if (Rt) Rt[s] = M::template put<C>(t);
+    }
+}
+
+}  // namespace exsum

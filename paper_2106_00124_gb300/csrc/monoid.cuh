@@ -11,6 +11,13 @@
 //   BF16   +    bf16 bits  fp32 pair (hi, lo)     fp32 (hi+lo)       fp32 pair fp32
 //   *      max  as above   the input's value type, identity INT_MIN / -inf
 //
+// Each monoid has two accumulators: acc_t for long reductions (carries) and
+// loc_t for short local scans over at most a few dozen elements (windows of
+// BDBS, the in-segment part of the dimension-1 step).  They differ only for
+// floating-point +, where loc_t is plain fp32: a short scan of values of
+// similar size adds an error far below the compensated carries it is added
+// to.
+//
 // Integer + and max are exact under any regrouping, so integer and max
 // results are bit-exact.  Floating-point + carries its running sums as an
 // unevaluated pair hi + lo (Knuth's TwoSum), so long reductions -- carries
@@ -61,12 +68,19 @@ struct MonIntAdd {
     using out_t = T;
     using acc_t = T;
     using car_t = T;
+    using loc_t = T;
     static constexpr bool compensated = false;
     __device__ __forceinline__ static acc_t id() { return (T)0; }
     __device__ __forceinline__ static acc_t op(acc_t a, acc_t b) { return (T)((U)a + (U)b); }
     __device__ __forceinline__ static acc_t get(T v) { return v; }
     template <class S>
     __device__ __forceinline__ static S put(acc_t a) { return a; }
+    __device__ __forceinline__ static loc_t lid() { return id(); }
+    __device__ __forceinline__ static loc_t lop(loc_t a, loc_t b) { return op(a, b); }
+    __device__ __forceinline__ static loc_t lget(T v) { return v; }
+    __device__ __forceinline__ static acc_t widen(loc_t v) { return v; }
+    template <class S>
+    __device__ __forceinline__ static S lput(loc_t a) { return a; }
 };
 
 // --- integer max ---------------------------------------------------------------
@@ -76,12 +90,19 @@ struct MonIntMax {
     using out_t = T;
     using acc_t = T;
     using car_t = T;
+    using loc_t = T;
     static constexpr bool compensated = false;
     __device__ __forceinline__ static acc_t id() { return (T)MINV; }
     __device__ __forceinline__ static acc_t op(acc_t a, acc_t b) { return a > b ? a : b; }
     __device__ __forceinline__ static acc_t get(T v) { return v; }
     template <class S>
     __device__ __forceinline__ static S put(acc_t a) { return a; }
+    __device__ __forceinline__ static loc_t lid() { return id(); }
+    __device__ __forceinline__ static loc_t lop(loc_t a, loc_t b) { return op(a, b); }
+    __device__ __forceinline__ static loc_t lget(T v) { return v; }
+    __device__ __forceinline__ static acc_t widen(loc_t v) { return v; }
+    template <class S>
+    __device__ __forceinline__ static S lput(loc_t a) { return a; }
 };
 
 // --- floating-point + with compensated accumulation -----------------------------
@@ -91,9 +112,19 @@ struct MonFloatAdd {
     using out_t = float;
     using acc_t = f2;
     using car_t = f2;
+    using loc_t = float;
     static constexpr bool compensated = true;
     __device__ __forceinline__ static acc_t id() { f2 z; z.hi = 0.f; z.lo = 0.f; return z; }
     __device__ __forceinline__ static acc_t op(acc_t a, acc_t b) { return f2_add(a, b); }
+    // Local (short-range) arithmetic: plain fp32.
+    __device__ __forceinline__ static loc_t lid() { return 0.f; }
+    __device__ __forceinline__ static loc_t lop(loc_t a, loc_t b) { return __fadd_rn(a, b); }
+    __device__ __forceinline__ static loc_t lget(float v) { return v; }
+    __device__ __forceinline__ static loc_t lget(uint16_t v) { return bf16_bits_to_float(v); }
+    __device__ __forceinline__ static loc_t lget(f2 v) { return __fadd_rn(v.hi, v.lo); }
+    __device__ __forceinline__ static acc_t widen(loc_t v) { f2 r; r.hi = v; r.lo = 0.f; return r; }
+    template <class S>
+    __device__ __forceinline__ static S lput(loc_t a);
     __device__ __forceinline__ static acc_t get(float v) { f2 r; r.hi = v; r.lo = 0.f; return r; }
     __device__ __forceinline__ static acc_t get(uint16_t v) { return get(bf16_bits_to_float(v)); }
     __device__ __forceinline__ static acc_t get(f2 v) { return v; }
@@ -103,6 +134,18 @@ struct MonFloatAdd {
 template <>
 template <>
 __device__ __forceinline__ float MonFloatAdd<float>::put<float>(f2 a) { return __fadd_rn(a.hi, a.lo); }
+template <>
+template <>
+__device__ __forceinline__ float MonFloatAdd<float>::lput<float>(float a) { return a; }
+template <>
+template <>
+__device__ __forceinline__ f2 MonFloatAdd<float>::lput<f2>(float a) { f2 r; r.hi = a; r.lo = 0.f; return r; }
+template <>
+template <>
+__device__ __forceinline__ float MonFloatAdd<uint16_t>::lput<float>(float a) { return a; }
+template <>
+template <>
+__device__ __forceinline__ f2 MonFloatAdd<uint16_t>::lput<f2>(float a) { f2 r; r.hi = a; r.lo = 0.f; return r; }
 template <>
 template <>
 __device__ __forceinline__ f2 MonFloatAdd<float>::put<f2>(f2 a) { return a; }
@@ -120,6 +163,7 @@ struct MonFloatMax {
     using out_t = float;
     using acc_t = float;
     using car_t = float;
+    using loc_t = float;
     static constexpr bool compensated = false;
     __device__ __forceinline__ static acc_t id() { return -__int_as_float(0x7f800000); }
     __device__ __forceinline__ static acc_t op(acc_t a, acc_t b) { return fmaxf(a, b); }
@@ -127,6 +171,13 @@ struct MonFloatMax {
     __device__ __forceinline__ static acc_t get(uint16_t v) { return bf16_bits_to_float(v); }
     template <class S>
     __device__ __forceinline__ static S put(acc_t a) { return a; }
+    __device__ __forceinline__ static loc_t lid() { return id(); }
+    __device__ __forceinline__ static loc_t lop(loc_t a, loc_t b) { return op(a, b); }
+    template <class V>
+    __device__ __forceinline__ static loc_t lget(V v) { return get(v); }
+    __device__ __forceinline__ static acc_t widen(loc_t v) { return v; }
+    template <class S>
+    __device__ __forceinline__ static S lput(loc_t a) { return a; }
 };
 
 using M_I32_ADD = MonIntAdd<int32_t, uint32_t>;

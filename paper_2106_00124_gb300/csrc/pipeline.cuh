@@ -11,7 +11,7 @@
 #include <stdint.h>
 #include <string.h>
 
-#include "kernels_lines.cuh"
+#include "kernels_fast.cuh"
 
 namespace exsum {
 
@@ -79,11 +79,59 @@ struct Pipe {
     static constexpr size_t SLOT_SMEM_MAX = 96 * 1024;
 
     // ---- BDBS-Along-Dim over a view [O, n, I] -------------------------------------
+    using L_ = typename M::loc_t;
+    static constexpr int CONTIG_ROWS = sizeof(L_) > 4 ? 64 : 128;
+
+    template <class SIn, class SOut, int KMAX>
+    static void inc_fast(Ctx &cx, const SIn *src, SOut *dst, int64_t O, int64_t n, int64_t I,
+                         int64_t k)
+    {
+        if (I == 1) {
+            const int Lc = (int)(n < 128 ? n : 128);
+            const int nchunks = (int)cdiv(n, Lc);
+            const int WL = Lc + KMAX - 1;
+            const int W = WL | 1;
+            const uint32_t magic = (uint32_t)((((uint64_t)1 << 32) + WL - 1) / WL);
+            const size_t smem = (size_t)CONTIG_ROWS * W * sizeof(L_);
+            auto kern = k_inc_contig<M, SIn, SOut, KMAX, CONTIG_ROWS>;
+            if (smem > 48 * 1024)
+                cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            const int64_t nvirt = O * nchunks;
+            cx.before(TAG_INC, O * n);
+            kern<<<(unsigned)cdiv(nvirt, CONTIG_ROWS), CONTIG_ROWS, smem, cx.stream>>>(
+                src, dst, O, (int)n, (int)k, Lc, nchunks, W, magic, WL);
+            cx.check_launch();
+        } else {
+            int Lc = 128;
+            while (Lc > 2 * k && Lc > 32 && O * cdiv(n, Lc) * I < 152 * 1024) Lc >>= 1;
+            if (Lc > n) Lc = (int)n;
+            const int nchunks = (int)cdiv(n, Lc);
+            const int64_t total = O * nchunks * I;
+            cx.before(TAG_INC, O * n * I);
+            k_inc_strided<M, SIn, SOut, KMAX><<<(unsigned)cdiv(total, 128), 128, 0, cx.stream>>>(
+                src, dst, O, (int)n, I, (int)k, Lc, nchunks);
+            cx.check_launch();
+        }
+    }
+
     template <class SIn, class SOut>
     static void inc_pass(Ctx &cx, const SIn *src, SOut *dst, int64_t O, int64_t n, int64_t I,
                          int64_t k)
     {
         if (!cx.ok()) return;
+        if (k <= 32 && n < (1ll << 30)) {
+            if (cx.dry) return;
+            if (k <= 4)
+                inc_fast<SIn, SOut, 4>(cx, src, dst, O, n, I, k);
+            else if (k <= 8)
+                inc_fast<SIn, SOut, 8>(cx, src, dst, O, n, I, k);
+            else if (k <= 16)
+                inc_fast<SIn, SOut, 16>(cx, src, dst, O, n, I, k);
+            else
+                inc_fast<SIn, SOut, 32>(cx, src, dst, O, n, I, k);
+            return;
+        }
+        // Large boxes: per-thread suffix slots in shared or global memory.
         int threads = INC_THREADS;
         while (threads > 32 && (size_t)k * threads * sizeof(A) > SLOT_SMEM_MAX) threads >>= 1;
         const bool global_slots = (size_t)k * threads * sizeof(A) > SLOT_SMEM_MAX;
@@ -109,24 +157,24 @@ struct Pipe {
     static void colsum(Ctx &cx, const SIn *X, CAR *G, int64_t n1, int64_t Mc)
     {
         if (!cx.ok()) return;
-        int64_t S = cdiv(65536, Mc);
-        if (S > n1) S = n1;
+        int64_t S = cdiv(152 * 2048, Mc);
+        if (S > cdiv(n1, 8)) S = cdiv(n1, 8);
         if (S < 1) S = 1;
         const int64_t L = cdiv(n1, S);
         S = cdiv(n1, L);
         if (S == 1) {
             if (cx.dry) return;
             cx.before(TAG_REDUCE, n1 * Mc);
-            k_reduce_seg<M, SIn><<<(unsigned)cdiv(Mc, 256), 256, 0, cx.stream>>>(X, G, nullptr, n1,
-                                                                                  Mc, L, 1, 0);
+            k_reduce_seg2<M, SIn><<<(unsigned)cdiv(Mc, 256), 256, 0, cx.stream>>>(X, G, nullptr, n1,
+                                                                                   Mc, L, 1, 0);
             cx.check_launch();
             return;
         }
         CAR *Rx = cx.take<CAR>(S * Mc);
         if (cx.dry || !cx.ok()) return;
         cx.before(TAG_REDUCE, n1 * Mc);
-        k_reduce_seg<M, SIn><<<(unsigned)cdiv(S * Mc, 256), 256, 0, cx.stream>>>(X, Rx, nullptr, n1,
-                                                                                  Mc, L, S, 0);
+        k_reduce_seg2<M, SIn><<<(unsigned)cdiv(S * Mc, 256), 256, 0, cx.stream>>>(X, Rx, nullptr, n1,
+                                                                                   Mc, L, S, 0);
         cx.check_launch();
         cx.before(TAG_SUMSEG, S * Mc);
         if (Mc >= 1024)
@@ -137,12 +185,16 @@ struct Pipe {
     }
 
     // ---- dimension-1 step: prefix/suffix along dim 1 + contributions --------------------
+    static constexpr int CT_NT = 256, CT_V = 16, CT_L = CT_NT * CT_V;  // contiguous segment
+
     template <class SH, class SOut>
     static void exline_stage(Ctx &cx, const SH *H, const CAR *T, SOut *out, int64_t n1,
                              int64_t Mc, int64_t k1)
     {
         if (!cx.ok()) return;
-        const int64_t S = cdiv(n1, EXL);
+        const bool contig = (Mc == 1);
+        const int64_t L = contig ? CT_L : EXL;
+        const int64_t S = cdiv(n1, L);
         const CAR *Q = T;
         int64_t qs = 0;
         if (S > 1) {
@@ -153,10 +205,14 @@ struct Pipe {
             CAR *SR = blk ? cx.take<CAR>(S * Mc) : nullptr;
             if (cx.dry || !cx.ok()) return;
             cx.before(TAG_REDUCE, n1 * Mc);
-            k_reduce_seg<M, SH><<<(unsigned)cdiv(S * Mc, 256), 256, 0, cx.stream>>>(
-                H, R, Rt, n1, Mc, EXL, S, k1 % EXL);
+            if (contig)
+                k_reduce_seg_contig<M, SH, CT_NT, CT_V><<<(unsigned)S, CT_NT, 0, cx.stream>>>(
+                    H, R, Rt, n1, k1 % L);
+            else
+                k_reduce_seg2<M, SH><<<(unsigned)cdiv(S * Mc, 256), 256, 0, cx.stream>>>(
+                    H, R, Rt, n1, Mc, L, S, k1 % L);
             cx.check_launch();
-            const int64_t qoff = 1 + k1 / EXL;
+            const int64_t qoff = 1 + k1 / L;
             cx.before(TAG_CARRY, S * Mc);
             if (blk)
                 k_carry_blk<M, 1024><<<(unsigned)Mc, 1024, 0, cx.stream>>>(R, Rt, T, Qb, SR, Mc, S,
@@ -170,8 +226,12 @@ struct Pipe {
         }
         if (cx.dry || !cx.ok()) return;
         cx.before(TAG_EXLINE, n1 * Mc);
-        k_exline<M, SH, SOut, EXL><<<(unsigned)cdiv(S * Mc, 128), 128, 0, cx.stream>>>(
-            H, Q, qs, out, n1, Mc, k1, S);
+        if (contig)
+            k_exline_contig<M, SH, SOut, CT_NT, CT_V><<<(unsigned)S, CT_NT, 0, cx.stream>>>(
+                H, Q, out, n1, k1);
+        else
+            k_exline2<M, SH, SOut, EXL><<<(unsigned)cdiv(S * Mc, 128), 128, 0, cx.stream>>>(
+                H, Q, qs, out, n1, Mc, k1, S);
         cx.check_launch();
     }
 

@@ -33,6 +33,12 @@ CASES = [
     ((5, 6, 7, 8), (2, 3, 4, 5)),
     ((3, 4, 5, 3, 4), (1, 2, 5, 3, 2)),
     ((2, 2, 2, 2, 2, 2, 2, 3), (1, 2, 1, 2, 2, 1, 2, 3)),
+    ((300000,), (4500,)),
+    ((300000,), (32,)),
+    ((5000, 3), (100, 2)),
+    ((3, 517), (2, 32)),
+    ((70, 300), (33, 31)),
+    ((7, 129, 131), (7, 17, 9)),
 ]
 
 
