@@ -128,6 +128,35 @@ int exsum_excluded(const void *in, void *out, int d, const int64_t *shape, const
 int exsum_excluded_ws(const void *in, void *out, int d, const int64_t *shape, const int64_t *k,
                       int op, int dtype, void *workspace, size_t workspace_bytes, void *stream);
 
+/*
+ * Excluded sums without any allocation.  The paper has no counterpart; this
+ * entry point exists for callers that cannot allocate device memory when
+ * they need the result -- a plugin inside a host framework that owns the
+ * device-memory budget, a real-time loop that cannot afford cudaMalloc's
+ * implicit synchronisation, a deployment whose allocations are fixed at
+ * start-up.  It runs exactly the exsum_excluded pipeline on a scratch
+ * buffer built into the library image: a static device array of
+ * EXSUM_NOALLOC_SCRATCH_BYTES bytes that every GPU loading the library
+ * holds until the process exits.  The caller still owns and passes `in` and
+ * `out` (device pointers, as for exsum_excluded).
+ *   - Problems whose workspace (exsum_workspace_bytes(..., excluded = 1))
+ *     exceeds EXSUM_NOALLOC_SCRATCH_BYTES are rejected with EXSUM_ENOMEM
+ *     before any work is queued; invalid arguments give EXSUM_EINVAL.
+ *   - It calls no cudaMalloc, cudaFree or allocating library routine
+ *     (keep the launch trace off, its default, when calling it).
+ *   - The first call on a device looks up the device address of the buffer
+ *     (cudaGetSymbolAddress, with that device current); make that first
+ *     call before any stream capture on that device.
+ *   - All calls on a device share the one buffer, and a call leaves its
+ *     intermediates there; the pipeline writes every scratch word before it
+ *     reads it, so nothing needs clearing between calls.  Calls whose work
+ *     overlaps on the GPU (different streams, or different host threads
+ *     without ordering) race on the buffer; order them on one stream.
+ */
+#define EXSUM_NOALLOC_SCRATCH_BYTES (64u << 20)
+int exsum_excluded_noalloc(const void *in, void *out, int d, const int64_t *shape, const int64_t *k,
+                           int op, int dtype, void *stream);
+
 /* Frees the library's cached per-device workspaces (synchronises the
  * device first).  Returns 0 or EXSUM_ECUDA. */
 int exsum_release_cached_workspace(void);

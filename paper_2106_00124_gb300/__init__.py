@@ -62,6 +62,8 @@ _SIG = {
     "exsum_excluded_ws": ([_P, _P, ctypes.c_int, _I64P, _I64P, ctypes.c_int, ctypes.c_int, _P,
                            ctypes.c_size_t, _P], ctypes.c_int),
     "exsum_release_cached_workspace": ([], ctypes.c_int),
+    "exsum_excluded_noalloc": ([_P, _P, ctypes.c_int, _I64P, _I64P, ctypes.c_int, ctypes.c_int, _P],
+                               ctypes.c_int),
     "exsum_trace_enable": ([ctypes.c_int], None),
     "exsum_trace_collect": ([ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                              ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_float),
@@ -147,6 +149,17 @@ def exsum_included_ws(in_ptr, out_ptr, d, shape, k, op, dtype, ws_ptr, ws_bytes,
 def exsum_excluded_ws(in_ptr, out_ptr, d, shape, k, op, dtype, ws_ptr, ws_bytes, stream=0):
     return _load().exsum_excluded_ws(in_ptr, out_ptr, int(d), _arr(shape), _arr(k), int(op),
                                      int(dtype), ws_ptr, int(ws_bytes), stream or None)
+
+
+# Size of the static scratch buffer behind exsum_excluded_noalloc (bytes).
+NOALLOC_SCRATCH_BYTES = 64 << 20
+
+
+def exsum_excluded_noalloc(in_ptr, out_ptr, d, shape, k, op, dtype, stream=0):
+    """Excluded sums on the library's static scratch buffer: no allocation.
+    For callers that cannot allocate device memory at call time."""
+    return _load().exsum_excluded_noalloc(in_ptr, out_ptr, int(d), _arr(shape), _arr(k), int(op),
+                                          int(dtype), stream or None)
 
 
 def exsum_release_cached_workspace():

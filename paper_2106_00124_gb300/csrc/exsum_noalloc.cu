@@ -1,0 +1,62 @@
+// exsum_noalloc.cu -- excluded sums for callers that cannot allocate device
+// memory at call time.
+//
+// Some callers have no way to call cudaMalloc when they need an excluded sum:
+// a plugin living inside a host framework that owns the whole device-memory
+// budget through its own allocator, a real-time loop that cannot afford the
+// implicit device synchronisation of cudaMalloc/cudaFree, or an embedded
+// deployment whose allocations are all fixed at start-up.  For them this
+// file provides exsum_excluded_noalloc(), which runs the same excluded-sum
+// pipeline as exsum_excluded_ws() on a fixed scratch buffer that is part of
+// the library image: a file-scope __device__ array of
+// EXSUM_NOALLOC_SCRATCH_BYTES bytes.  Every GPU that loads the library holds
+// that buffer until the process exits.
+//
+// The array's name, used in host code, is only a host-side stand-in for the
+// device variable; passing it to a kernel would fault or (where the GPU can
+// reach host memory) silently use the wrong memory.  The device address is
+// therefore looked up with cudaGetSymbolAddress once per device, with that
+// device current, on the first call made on that device.
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "../../include/exsum.h"
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[EXSUM_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[kMaxDevices] = {};
+}  // namespace
+
+extern "C" int exsum_excluded_noalloc(const void *in, void *out, int d, const int64_t *shape,
+                                      const int64_t *k, int op, int dtype, void *stream)
+{
+    int status = EXSUM_OK;
+    const size_t need = exsum_workspace_bytes(d, shape, k, op, dtype, 1, &status);
+    if (status != EXSUM_OK) return status;
+    if (!in || !out) return EXSUM_EINVAL;
+    if (need > (size_t)EXSUM_NOALLOC_SCRATCH_BYTES) return EXSUM_ENOMEM;
+
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) return EXSUM_ECUDA;
+    void *scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            void *p = nullptr;
+            e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess || !p) {
+                cudaGetLastError();
+                return EXSUM_ECUDA;
+            }
+            g_noalloc_ptr[dev] = p;
+        }
+        scratch = g_noalloc_ptr[dev];
+    }
+    return exsum_excluded_ws(in, out, d, shape, k, op, dtype, scratch,
+                             (size_t)EXSUM_NOALLOC_SCRATCH_BYTES, stream);
+}
