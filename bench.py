@@ -12,9 +12,10 @@ line (rank 0).
 Timing: the step is captured once into a CUDA graph; each replay is
 bracketed by CUDA events on the stream it runs on, and between steps a
 256 MiB buffer is written to flush the 129 MB L2, outside the timed spans.
-`value` sums the K step spans; the per-kernel roofline comes from the
-library's launch trace (event-record nodes around every kernel node of the
-graph) read after each replay of the same timed region.  `e2e` calls the C
+`value` sums the K step spans.  The per-kernel roofline comes from a second
+capture of the same step with the library's launch trace on (event-record
+nodes around every kernel node), replayed K more times inside the timed
+region and read back after each replay.  `e2e` calls the C
 ABI directly (no graph) with host input and output buffers.
 """
 
@@ -51,6 +52,9 @@ def parse_args(argv=None):
     p.add_argument("--workload", default=DEFAULT_WORKLOAD)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--profile-once", action="store_true",
+                   help="run the workload's excluded sum twice without graphs or timing "
+                        "(a small, self-ending command for ncu) and exit")
     return p.parse_args(argv)
 
 
@@ -229,17 +233,30 @@ def run_ours(args):
         step(sp)
     torch.cuda.synchronize()
 
-    # The step is captured once into a CUDA graph (all of its launches), with
-    # the launch trace on: each kernel node is bracketed by event-record nodes
-    # whose times are read back after every replay.
-    ex.exsum_trace_collect(clear=True)
-    graph = torch.cuda.CUDAGraph()
-    launches0 = ex.exsum_launch_count()
-    ex.exsum_trace_enable(True)
-    with torch.cuda.graph(graph):
-        step(torch.cuda.current_stream().cuda_stream)
-    ex.exsum_trace_enable(False)
-    launches_per_step = ex.exsum_launch_count() - launches0
+    # The step is captured once into a CUDA graph (all of its launches).  A
+    # second capture of the same step carries the launch trace: each kernel
+    # node is bracketed by event-record nodes, read back after every replay.
+    # Capture on a stream that has run the step once outside capture: the
+    # library creates the side stream of a caller stream on its first
+    # uncaptured call, and forks onto it under capture from then on.
+    cap_stream = torch.cuda.Stream(device)
+    cap_stream.wait_stream(stream)
+    with torch.cuda.stream(cap_stream):
+        step(cap_stream.cuda_stream)
+    cap_stream.synchronize()
+
+    def capture(traced):
+        g = torch.cuda.CUDAGraph()
+        ex.exsum_trace_collect(clear=True)
+        ex.exsum_trace_enable(traced)
+        l0 = ex.exsum_launch_count()
+        with torch.cuda.graph(g, stream=cap_stream):
+            step(cap_stream.cuda_stream)
+        ex.exsum_trace_enable(False)
+        return g, ex.exsum_launch_count() - l0
+
+    graph, launches_per_step = capture(False)
+    tgraph, _ = capture(True)
     for _ in range(args.warmup):
         flush.fill_(1)
         graph.replay()
@@ -253,15 +270,19 @@ def run_ours(args):
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    trace = []
     for i in range(args.steps):
         flush.fill_(1)
         evs[i][0].record(stream)
         graph.replay()
         evs[i][1].record(stream)
-        torch.cuda.synchronize()
-        trace.extend(ex.exsum_trace_collect(cap=256, clear=False))
     torch.cuda.synchronize()
+    # Per-kernel durations: the traced graph over the same number of steps.
+    trace = []  # (position of the launch in the step, kernel, level, elements, ms)
+    for i in range(args.steps):
+        flush.fill_(1)
+        tgraph.replay()
+        torch.cuda.synchronize()
+        trace.extend((j,) + rec for j, rec in enumerate(ex.exsum_trace_collect(cap=256, clear=False)))
     launches = launches_per_step * args.steps
     if world > 1:
         torch.distributed.barrier()
@@ -276,15 +297,15 @@ def run_ours(args):
     # ---- per-kernel roofline from the trace ---------------------------------------------------
     peak, peak_kind = measured_peaks()
     groups = {}
-    for name, level, elems, ms in trace:
-        g = groups.setdefault((name, level, elems), [0, 0.0])
+    for pos, name, level, elems, ms in trace:
+        g = groups.setdefault((pos, name, level, elems), [0, 0.0])
         g[0] += 1
         g[1] += ms
     passes = []
-    for (name, level, elems), (cnt, tot) in groups.items():
+    for (pos, name, level, elems), (cnt, tot) in groups.items():
         mean_ms = tot / cnt
         b = pass_bytes(name, level, elems, dtype)
-        passes.append({"kernel": name, "level": level, "elems": elems, "launches": cnt,
+        passes.append({"pos": pos, "kernel": name, "level": level, "elems": elems, "launches": cnt,
                        "mean_us": round(mean_ms * 1e3, 3), "share": 0.0,
                        "algo_bytes": b, "achieved_gbs": round(b / (mean_ms * 1e-3) / 1e9, 1)})
     total_kernel_ms = sum(p["mean_us"] * p["launches"] for p in passes) or 1.0
@@ -446,8 +467,28 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_profile_once(args):
+    """Two plain calls of the workload's excluded sum, for profilers."""
+    import numpy as np
+    import torch
+
+    import paper_2106_00124_gb300 as ex
+    from paper_2106_00124_gb300 import synth
+    torch.cuda.set_device(0)
+    dev, _, spec = synth.workload_input(args.workload)
+    x = (torch.from_numpy(np.ascontiguousarray(dev).view(np.int16)).view(torch.bfloat16)
+         if spec["dtype"] == "bf16" else torch.from_numpy(np.ascontiguousarray(dev))).cuda()
+    for _ in range(2):
+        ex.excluded(x, spec["k"], spec["op"])
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_once": args.workload, "launches": ex.exsum_launch_count()}))
+
+
 def main(argv=None):
     args = parse_args(argv)
+    if args.profile_once:
+        run_profile_once(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

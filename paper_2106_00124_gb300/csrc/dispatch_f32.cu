@@ -5,13 +5,13 @@ namespace exsum {
 
 int dispatch_f32(int op, int excluded, const void *in, void *out, int d, const int64_t *n,
                    const int64_t *k, void *ws, size_t ws_bytes, cudaStream_t stream,
-                   size_t *ws_needed, cudaError_t *cuda_err)
+                   size_t *ws_needed, cudaError_t *cuda_err, const Aux *aux)
 {
     if (op == OP_ADD)
         return Pipe<M_F32_ADD>::run(excluded, in, out, d, n, k, ws, ws_bytes, stream, ws_needed,
-                                     cuda_err);
+                                     cuda_err, aux);
     return Pipe<M_F32_MAX>::run(excluded, in, out, d, n, k, ws, ws_bytes, stream, ws_needed,
-                                 cuda_err);
+                                 cuda_err, aux);
 }
 
 }  // namespace exsum

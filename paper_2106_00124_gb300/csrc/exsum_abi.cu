@@ -13,13 +13,13 @@
 
 namespace exsum {
 int dispatch_i32(int, int, const void *, void *, int, const int64_t *, const int64_t *, void *,
-                 size_t, cudaStream_t, size_t *, cudaError_t *);
+                 size_t, cudaStream_t, size_t *, cudaError_t *, const Aux *);
 int dispatch_i64(int, int, const void *, void *, int, const int64_t *, const int64_t *, void *,
-                 size_t, cudaStream_t, size_t *, cudaError_t *);
+                 size_t, cudaStream_t, size_t *, cudaError_t *, const Aux *);
 int dispatch_f32(int, int, const void *, void *, int, const int64_t *, const int64_t *, void *,
-                 size_t, cudaStream_t, size_t *, cudaError_t *);
+                 size_t, cudaStream_t, size_t *, cudaError_t *, const Aux *);
 int dispatch_bf16(int, int, const void *, void *, int, const int64_t *, const int64_t *, void *,
-                  size_t, cudaStream_t, size_t *, cudaError_t *);
+                  size_t, cudaStream_t, size_t *, cudaError_t *, const Aux *);
 }  // namespace exsum
 
 static thread_local int g_last_cuda_error = 0;
@@ -102,18 +102,55 @@ static int validate(int d, const int64_t *shape, const int64_t *k, int op, int d
     return EXSUM_OK;
 }
 
+// ---- side streams: one (stream, fork event, join event) per (device, caller stream) -------------
+namespace {
+std::mutex g_aux_mu;
+std::map<std::pair<int, void *>, exsum::Aux> g_aux;
+}  // namespace
+
+// The side stream of the caller's stream, created on first use outside any
+// stream capture; nullptr (run everything on the caller's stream) otherwise.
+static const exsum::Aux *aux_for(void *stream)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lock(g_aux_mu);
+    auto key = std::make_pair(dev, stream);
+    auto it = g_aux.find(key);
+    if (it != g_aux.end()) return it->second.side ? &it->second : nullptr;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing((cudaStream_t)stream, &cs) != cudaSuccess ||
+        cs != cudaStreamCaptureStatusNone) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    exsum::Aux a;
+    if (cudaStreamCreateWithFlags(&a.side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&a.fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&a.join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        a = exsum::Aux();
+    }
+    g_aux[key] = a;
+    return a.side ? &g_aux[key] : nullptr;
+}
+
 static int run(int excluded, const void *in, void *out, int d, const int64_t *shape,
                const int64_t *k, int op, int dtype, void *ws, size_t ws_bytes, void *stream,
-               size_t *need)
+               size_t *need, bool allow_fork = true)
 {
     cudaError_t ce = cudaSuccess;
     int rc;
     cudaStream_t st = (cudaStream_t)stream;
+    const exsum::Aux *aux = (in && excluded && allow_fork) ? aux_for(stream) : nullptr;
     switch (dtype) {
-    case EXSUM_I32: rc = exsum::dispatch_i32(op, excluded, in, out, d, shape, k, ws, ws_bytes, st, need, &ce); break;
-    case EXSUM_I64: rc = exsum::dispatch_i64(op, excluded, in, out, d, shape, k, ws, ws_bytes, st, need, &ce); break;
-    case EXSUM_F32: rc = exsum::dispatch_f32(op, excluded, in, out, d, shape, k, ws, ws_bytes, st, need, &ce); break;
-    default: rc = exsum::dispatch_bf16(op, excluded, in, out, d, shape, k, ws, ws_bytes, st, need, &ce); break;
+    case EXSUM_I32: rc = exsum::dispatch_i32(op, excluded, in, out, d, shape, k, ws, ws_bytes, st, need, &ce, aux); break;
+    case EXSUM_I64: rc = exsum::dispatch_i64(op, excluded, in, out, d, shape, k, ws, ws_bytes, st, need, &ce, aux); break;
+    case EXSUM_F32: rc = exsum::dispatch_f32(op, excluded, in, out, d, shape, k, ws, ws_bytes, st, need, &ce, aux); break;
+    default: rc = exsum::dispatch_bf16(op, excluded, in, out, d, shape, k, ws, ws_bytes, st, need, &ce, aux); break;
     }
     if (rc == EXSUM_ECUDA) g_last_cuda_error = (int)ce;
     return rc;
@@ -314,6 +351,24 @@ const char *exsum_kernel_name(int tag)
 }
 
 int64_t exsum_launch_count(void) { return g_launches.load(); }
+
+}  // extern "C"
+
+namespace exsum {
+// exsum_excluded_ws without the side stream: everything on `stream`, no
+// stream or event is ever created (used by the allocation-free entry point).
+int excluded_ws_serial(const void *in, void *out, int d, const int64_t *shape, const int64_t *k,
+                       int op, int dtype, void *workspace, size_t workspace_bytes, void *stream)
+{
+    int rc = validate(d, shape, k, op, dtype);
+    if (rc) return rc;
+    if (!in || !out) return EXSUM_EINVAL;
+    return run(1, in, out, d, shape, k, op, dtype, workspace, workspace_bytes, stream, nullptr,
+               false);
+}
+}  // namespace exsum
+
+extern "C" {
 
 int exsum_release_cached_workspace(void)
 {

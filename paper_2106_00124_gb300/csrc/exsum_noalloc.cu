@@ -25,6 +25,11 @@
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[EXSUM_NOALLOC_SCRATCH_BYTES];
 
+namespace exsum {
+int excluded_ws_serial(const void *in, void *out, int d, const int64_t *shape, const int64_t *k,
+                       int op, int dtype, void *workspace, size_t workspace_bytes, void *stream);
+}
+
 namespace {
 constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
@@ -57,6 +62,7 @@ extern "C" int exsum_excluded_noalloc(const void *in, void *out, int d, const in
         }
         scratch = g_noalloc_ptr[dev];
     }
-    return exsum_excluded_ws(in, out, d, shape, k, op, dtype, scratch,
-                             (size_t)EXSUM_NOALLOC_SCRATCH_BYTES, stream);
+    // Serial schedule: no side stream or event is created on this path.
+    return exsum::excluded_ws_serial(in, out, d, shape, k, op, dtype, scratch,
+                                     (size_t)EXSUM_NOALLOC_SCRATCH_BYTES, stream);
 }

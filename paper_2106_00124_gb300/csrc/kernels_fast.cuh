@@ -10,6 +10,8 @@
 // step and one combine (Combine-Along-Row).
 #pragma once
 
+#include <type_traits>
+
 #include "kernels_lines.cuh"
 
 namespace exsum {
@@ -73,45 +75,137 @@ k_inc_strided(const SIn *__restrict__ in, SOut *__restrict__ out, int64_t O, int
 // ---------------------------------------------------------------------------
 // BDBS-Along-Dim along the contiguous dimension (rows of length n).  A block
 // takes ROWS "virtual rows" (row, chunk of Lc outputs), stages each with its
-// k-1 halo into a padded shared-memory tile with coalesced loads, lets one
-// thread walk each virtual row from shared memory (odd row stride: the
-// threads of a warp hit distinct banks), writes results back in place and
-// stores them coalesced.
+// k-1 halo into a padded shared-memory tile with coalesced, batched loads,
+// lets one thread walk each virtual row from shared memory (odd row stride:
+// the threads of a warp hit distinct banks), writes results back in place
+// and stores them coalesced.
+//
+// With Rsum != nullptr the block also produces the dimension-1 segment
+// totals of its input that box-complement's carries need: its virtual rows
+// are then taken as groups of 32 consecutive dimension-1 coordinates (one
+// segment) of the same (row-within-slice, chunk), and for every staged core
+// position it reduces the group over dimension 1 -- Rsum[s][c] over the
+// whole segment and Rtail[s][c] over the segment's rows from offset r_tail
+// -- from the tile it has already loaded.  Rows are x1 * R1 + rr.
 // ---------------------------------------------------------------------------
 template <class M, class SIn, class SOut, int KMAX, int ROWS>
 __global__ void __launch_bounds__(ROWS)
 k_inc_contig(const SIn *__restrict__ in, SOut *__restrict__ out, int64_t nrows, int n, int k,
-             int Lc, int nchunks, int W, uint32_t wl_magic, int WL)
+             int Lc, int nchunks, int W, uint32_t wl_magic, int WL, int64_t n1, int64_t R1,
+             typename M::car_t *__restrict__ Rsum, typename M::car_t *__restrict__ Rtail,
+             int r_tail)
 {
     using Lt = typename M::loc_t;
+    using C = typename M::car_t;
+    constexpr int SEG = 32;
+    constexpr int UNR = 16;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Lt *tile = reinterpret_cast<Lt *>(smem_raw);
     __shared__ int64_t row_off[ROWS];   // global offset of position p0 of each tile row
     __shared__ int row_lim[ROWS];       // positions of the tile row that exist (n - p0)
-    const int64_t v0 = (int64_t)blockIdx.x * ROWS;        // first virtual row
-    const int64_t nvirt = nrows * nchunks;
     const int tid = threadIdx.x;
+    const bool sums = Rsum != nullptr;
     {
-        const int64_t vr = v0 + tid;
         int64_t off = 0;
         int lim = 0;
-        if (vr < nvirt) {
-            const int64_t row = vr / nchunks;
-            const int p0 = (int)(vr - row * nchunks) * Lc;
-            off = row * n + p0;
-            lim = n - p0;
+        if (!sums) {
+            const int64_t vr = (int64_t)blockIdx.x * ROWS + tid;
+            if (vr < nrows * nchunks) {
+                const int64_t row = vr / nchunks;
+                const int p0 = (int)(vr - row * nchunks) * Lc;
+                off = row * n + p0;
+                lim = n - p0;
+            }
+        } else {
+            // group = (segment, row-within-slice, chunk); SEG rows of dimension 1 per group
+            const int64_t grp = (int64_t)blockIdx.x * (ROWS / SEG) + tid / SEG;
+            const int64_t per_seg = R1 * nchunks;
+            const int64_t s = grp / per_seg;
+            const int64_t rem = grp - s * per_seg;
+            const int64_t rr = rem / nchunks;
+            const int ch = (int)(rem - rr * nchunks);
+            const int64_t x1 = s * SEG + (tid % SEG);
+            if (x1 < n1 && rr < R1) {
+                off = (x1 * R1 + rr) * n + (int64_t)ch * Lc;
+                lim = n - ch * Lc;
+            }
         }
         row_off[tid] = off;
         row_lim[tid] = lim;
     }
     __syncthreads();
     // Stage: tile row r holds positions p0 .. p0+WL-1 of its row (e past n).
-    for (int e = tid; e < ROWS * WL; e += ROWS) {
-        const int r = (int)__umulhi((uint32_t)e, wl_magic);
-        const int x = e - r * WL;
-        tile[r * W + x] = x < row_lim[r] ? M::lget(in[row_off[r] + x]) : M::lid();
+    if constexpr (std::is_same<SIn, Lt>::value && (sizeof(Lt) == 4 || sizeof(Lt) == 8)) {
+        // Same element type in global and shared memory: asynchronous copies,
+        // all of the block's loads in flight at once.
+        for (int e = tid; e < ROWS * WL; e += ROWS) {
+            const int r = (int)__umulhi((uint32_t)e, wl_magic);
+            const int x = e - r * WL;
+            Lt *dst = tile + r * W + x;
+            if (x < row_lim[r]) {
+                const uint32_t sdst = (uint32_t)__cvta_generic_to_shared(dst);
+                const size_t gsrc = __cvta_generic_to_global(in + row_off[r] + x);
+                if constexpr (sizeof(Lt) == 4)
+                    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sdst), "l"(gsrc));
+                else
+                    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sdst), "l"(gsrc));
+            } else {
+                *dst = M::lid();
+            }
+        }
+        asm volatile("cp.async.commit_group;\n" ::);
+        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    } else {
+        for (int e0 = tid; e0 < ROWS * WL; e0 += ROWS * UNR) {
+            Lt vals[UNR];
+#pragma unroll
+            for (int u = 0; u < UNR; ++u) {
+                const int e = e0 + u * ROWS;
+                vals[u] = M::lid();
+                if (e < ROWS * WL) {
+                    const int r = (int)__umulhi((uint32_t)e, wl_magic);
+                    const int x = e - r * WL;
+                    if (x < row_lim[r]) vals[u] = M::lget(in[row_off[r] + x]);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < UNR; ++u) {
+                const int e = e0 + u * ROWS;
+                if (e < ROWS * WL) {
+                    const int r = (int)__umulhi((uint32_t)e, wl_magic);
+                    tile[r * W + (e - r * WL)] = vals[u];
+                }
+            }
+        }
     }
     __syncthreads();
+    if (sums) {
+        // thread -> (group, core position); reduce the group's SEG rows
+        const int g = tid / SEG, x = tid % SEG;
+        const int64_t grp = (int64_t)blockIdx.x * (ROWS / SEG) + g;
+        const int64_t per_seg = R1 * nchunks;
+        const int64_t s = grp / per_seg;
+        const int64_t rem = grp - s * per_seg;
+        const int64_t rr = rem / nchunks;
+        const int ch = (int)(rem - rr * nchunks);
+        const int p = ch * Lc + x;
+        if (s * SEG < n1 && rr < R1 && x < Lc && p < n) {
+            Lt head = M::lid(), tail = M::lid();
+            const Lt *col = tile + g * SEG * W + x;
+#pragma unroll 8
+            for (int u = 0; u < SEG; ++u) {
+                const Lt v = col[u * W];
+                if (u < r_tail)
+                    head = M::lop(head, v);
+                else
+                    tail = M::lop(tail, v);
+            }
+            const int64_t c = rr * n + p;
+            const int64_t Mc = R1 * n;
+            Rsum[s * Mc + c] = M::template put<C>(M::op(M::widen(head), M::widen(tail)));
+            Rtail[s * Mc + c] = M::template put<C>(M::widen(tail));
+        }
+    }
     {
         const int len = min(Lc, row_lim[tid]);
         Lt *trow = tile + tid * W;
@@ -137,10 +231,18 @@ __device__ __forceinline__ typename M::acc_t reduce_rows(const SIn *__restrict__
 {
     typename M::acc_t acc = M::id();
     for (int64_t y0 = ya; y0 < yb; y0 += 32) {
-        const int64_t y1 = min(y0 + 32, yb);
         typename M::loc_t l = M::lid();
-#pragma unroll 8
-        for (int64_t y = y0; y < y1; ++y) l = M::lop(l, M::lget(col[y * Mc]));
+#pragma unroll
+        for (int b = 0; b < 32; b += 8) {
+            typename M::loc_t v[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int64_t y = y0 + b + j;
+                v[j] = y < yb ? M::lget(col[y * Mc]) : M::lid();
+            }
+#pragma unroll
+            for (int j = 0; j < 8; ++j) l = M::lop(l, v[j]);
+        }
         acc = M::op(acc, M::widen(l));
     }
     return acc;
@@ -176,7 +278,8 @@ k_reduce_seg2(const SIn *__restrict__ X, typename M::car_t *__restrict__ R,
 template <class M, class SIn, class SOut, int L>
 __global__ void __launch_bounds__(128)
 k_exline2(const SIn *__restrict__ H, const typename M::car_t *__restrict__ Q, int64_t qs,
-          SOut *__restrict__ out, int64_t n1, int64_t Mc, int64_t k1, int64_t S)
+          const typename M::car_t *__restrict__ T, SOut *__restrict__ out, int64_t n1, int64_t Mc,
+          int64_t k1, int64_t S)
 {
     using Lt = typename M::loc_t;
     const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -188,17 +291,26 @@ k_exline2(const SIn *__restrict__ H, const typename M::car_t *__restrict__ Q, in
     SOut *op_ = out + s0 * Mc + c;
     Lt P[L];
     Lt acc = M::lid();
-    const typename M::acc_t q = Q ? M::get(Q[s * qs + c]) : M::id();
+    typename M::acc_t q = Q ? M::get(Q[s * qs + c]) : M::id();
+    if (T) q = M::op(q, M::get(T[c]));
     Lt sacc = M::lid();
     if (s0 + L + k1 <= n1) {
+        // Both windows' loads issued before any use: one memory latency per thread.
+        Lt tv[L];
 #pragma unroll
         for (int t = 0; t < L; ++t) {
+            P[t] = M::lget(hp[t * Mc]);
+            tv[t] = M::lget(tp[t * Mc]);
+        }
+#pragma unroll
+        for (int t = 0; t < L; ++t) {
+            const Lt v = P[t];
             P[t] = acc;
-            acc = M::lop(acc, M::lget(hp[t * Mc]));
+            acc = M::lop(acc, v);
         }
 #pragma unroll
         for (int t = L - 1; t >= 0; --t) {
-            sacc = M::lop(M::lget(tp[t * Mc]), sacc);
+            sacc = M::lop(tv[t], sacc);
             op_[t * Mc] = M::template put<SOut>(M::op(q, M::widen(M::lop(P[t], sacc))));
         }
     } else {
@@ -257,6 +369,47 @@ k_exline_contig(const SIn *__restrict__ H, const typename M::car_t *__restrict__
 #pragma unroll
     for (int j = 0; j < V; ++j)
         if (s0 + j < n1) out[s0 + j] = M::template put<SOut>(M::op(q, M::widen(M::lop(pre[j], suf[j]))));
+}
+
+// ---------------------------------------------------------------------------
+// Carries from the dimension-1 segment totals of the input (view [n1, Mc],
+// segments of L rows): per segment s and column c
+//   Qa[s][c] = (+)_{s' < s} R[s'][c]  (+)  Rt[q][c] (+) (+)_{s' > q} R[s'][c],
+// q = s + qoff (the rows before the segment and the rows past its target
+// window), and the column total G[c] = (+)_s R[s][c].  Box-complement then
+// applies the included sums along dimensions 2..d to Qa; by linearity of the
+// reduction over boxes this equals the carries of the included tensor.
+// ---------------------------------------------------------------------------
+template <class M>
+__global__ void __launch_bounds__(256)
+k_carry_qa(const typename M::car_t *__restrict__ R, const typename M::car_t *__restrict__ Rt,
+           typename M::car_t *__restrict__ Qa, typename M::car_t *__restrict__ G, int64_t Mc,
+           int64_t S, int64_t qoff)
+{
+    using A = typename M::acc_t;
+    using C = typename M::car_t;
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= Mc) return;
+    // Backward: suffix totals SR[s] parked in Qa.
+    A acc = M::id();
+    for (int64_t s = S - 1; s >= 0; --s) {
+        acc = M::op(M::get(R[s * Mc + c]), acc);
+        if (Qa) Qa[s * Mc + c] = M::template put<C>(acc);
+    }
+    G[c] = M::template put<C>(acc);
+    if (!Qa) return;
+    A pc = M::id();
+    for (int64_t s = 0; s < S; ++s) {
+        const int64_t q = s + qoff;
+        A w = M::id();
+        if (q < S) {
+            w = M::get(Rt[q * Mc + c]);
+            if (q + 1 < S) w = M::op(w, M::get(Qa[(q + 1) * Mc + c]));
+        }
+        const A rs = M::get(R[s * Mc + c]);
+        Qa[s * Mc + c] = M::template put<C>(M::op(pc, w));
+        pc = M::op(pc, rs);
+    }
 }
 
 // Segment reductions of a single contiguous line: one block per segment of

@@ -1,0 +1,241 @@
+// kernels_flat.cuh -- the contiguous-dimension pass and the dimension-1 step
+// with every global access vectorised or asynchronous.
+#pragma once
+
+#include <string.h>
+
+#include <type_traits>
+
+#include "kernels_fast.cuh"
+
+namespace exsum {
+
+template <class T>
+__device__ __forceinline__ void cp_async_elem(T *sdst, const T *gsrc)
+{
+    const uint32_t s = (uint32_t)__cvta_generic_to_shared(sdst);
+    const size_t g = __cvta_generic_to_global(gsrc);
+    if constexpr (sizeof(T) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(g));
+    else if constexpr (sizeof(T) == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(g));
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(g));
+}
+// Four consecutive elements starting at p (16-byte-aligned vector access when
+// `vec`, else scalar), converted to the local accumulator type.
+template <class M, class SIn>
+__device__ __forceinline__ void load4(const SIn *p, bool vec, int valid, typename M::loc_t v[4])
+{
+    if (vec) {
+        SIn t[4];
+        if constexpr (sizeof(SIn) * 4 == 16) {
+            const uint4 r = *reinterpret_cast<const uint4 *>(p);
+            memcpy(t, &r, 16);
+        } else if constexpr (sizeof(SIn) * 4 == 8) {
+            const uint2 r = *reinterpret_cast<const uint2 *>(p);
+            memcpy(t, &r, 8);
+        } else {
+            const uint4 r0 = reinterpret_cast<const uint4 *>(p)[0];
+            const uint4 r1 = reinterpret_cast<const uint4 *>(p)[1];
+            memcpy(t, &r0, 16);
+            memcpy(t + 2, &r1, 16);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) v[i] = M::lget(t[i]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) v[i] = i < valid ? M::lget(p[i]) : M::lid();
+    }
+}
+
+template <class M, class SOut>
+__device__ __forceinline__ void store4(SOut *p, bool vec, int valid, const typename M::loc_t v[4])
+{
+    SOut t[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) t[i] = M::template lput<SOut>(v[i]);
+    if (vec) {
+        if constexpr (sizeof(SOut) * 4 == 16) {
+            uint4 r;
+            memcpy(&r, t, 16);
+            *reinterpret_cast<uint4 *>(p) = r;
+        } else {
+            uint4 r0, r1;
+            memcpy(&r0, t, 16);
+            memcpy(&r1, t + 2, 16);
+            reinterpret_cast<uint4 *>(p)[0] = r0;
+            reinterpret_cast<uint4 *>(p)[1] = r1;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            if (i < valid) p[i] = t[i];
+    }
+}
+
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\n" ::);
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+// ---------------------------------------------------------------------------
+// BDBS-Along-Dim along the contiguous dimension, on the flattened tensor.
+//
+// A warp owns a chunk of 128 consecutive elements of one "plane" (M1
+// consecutive elements; planes hold whole rows of length n); lane l owns
+// elements 4l .. 4l+3 of the chunk and the warp also stages the 32 elements
+// after it (the halo: k-1 <= 31 more are needed).  Each output x sums its
+// window s[x .. x+k) with the window cut at the end of its row, i.e. over
+// j < min(k, n - pos(x)), which is the clipped box of Sec. 2; the sum is
+// unrolled to KMAX >= k with per-term predicates (register-only, no dynamic
+// indexing).  For the small k this pass uses, this costs KMAX operations per
+// element, against three for a sequential BDBS-1D walk, but every load and
+// store is a coalesced 16-byte access and no thread walks a row serially.
+//
+// The warps of a block walk the 32 planes of one dimension-1 segment
+// (4 planes each) at the same chunk position.  With Rsum != nullptr each lane
+// also adds its 4 input elements over those planes -- the whole segment into
+// Rsum[s][c], the planes from offset r_tail on into Rtail[s][c] -- the
+// segment totals the box-complement carries need.
+// ---------------------------------------------------------------------------
+template <class M, class SIn, class SOut, int KMAX>
+__global__ void __launch_bounds__(256)
+k_inc_flat(const SIn *__restrict__ in, SOut *__restrict__ out, int64_t N, int64_t n1, int64_t M1,
+           int64_t n, int k, int64_t nq, typename M::car_t *__restrict__ Rsum,
+           typename M::car_t *__restrict__ Rtail, int r_tail)
+{
+    using Lt = typename M::loc_t;
+    using C = typename M::car_t;
+    constexpr int SEG = 32, WARPS = 8, CH = 128, HALO = 32;
+    __shared__ Lt buf[WARPS][CH + HALO];
+    __shared__ Lt red_h[WARPS][CH], red_t[WARPS][CH];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t q = blockIdx.x % nq;          // chunk position in the plane
+    const int64_t s = blockIdx.x / nq;          // dimension-1 segment
+    const int64_t c0 = q * CH;                  // first column of the chunk
+    const bool sums = Rsum != nullptr;
+    Lt hs[4], ts[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) hs[i] = ts[i] = M::lid();
+    // row position of this lane's first column (the same in every plane)
+    const int64_t col = c0 + 4 * lane;
+    const int pos0 = (int)(col % n);
+    Lt *sb = buf[warp];
+    for (int u = warp; u < SEG; u += WARPS) {
+        const int64_t x1 = s * SEG + u;
+        if (x1 >= n1) break;
+        const int64_t base = x1 * M1 + c0;          // flat index of the chunk start
+        const int64_t lim_c = min(M1 - c0, N - base); // elements of the chunk that exist
+        // stage the chunk and its halo (e past the plane or the tensor)
+        Lt v[4];
+        const int valid = (int)max((int64_t)0, min((int64_t)4, lim_c - 4 * lane));
+        const SIn *src = in + base + 4 * lane;
+        const bool vin = valid == 4 && (((uintptr_t)src) & (4 * sizeof(SIn) - 1)) == 0;
+        load4<M>(src, vin, valid, v);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) sb[4 * lane + i] = v[i];
+        sb[CH + lane] = (CH + lane < lim_c) ? M::lget(in[base + CH + lane]) : M::lid();
+        __syncwarp();
+        if (sums) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                if (u < r_tail)
+                    hs[i] = M::lop(hs[i], v[i]);
+                else
+                    ts[i] = M::lop(ts[i], v[i]);
+            }
+        }
+        Lt st[4 + KMAX - 1];
+#pragma unroll
+        for (int j = 0; j < 4 + KMAX - 1; ++j) st[j] = (4 * lane + j < CH + HALO) ? sb[4 * lane + j] : M::lid();
+        __syncwarp();
+        Lt o[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            int p = pos0 + i;
+            while (p >= n) p -= (int)n;
+            const int lim = min(k, (int)n - p);
+            Lt acc = st[i];
+#pragma unroll
+            for (int j = 1; j < KMAX; ++j)
+                if (j < lim) acc = M::lop(acc, st[i + j]);
+            o[i] = acc;
+        }
+        SOut *dst = out + base + 4 * lane;
+        const bool vout = valid == 4 && (((uintptr_t)dst) & (4 * sizeof(SOut) - 1)) == 0;
+        if (valid > 0) store4<M>(dst, vout, valid, o);
+    }
+    if (sums) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            red_h[warp][4 * lane + i] = hs[i];
+            red_t[warp][4 * lane + i] = ts[i];
+        }
+        __syncthreads();
+        if (threadIdx.x < CH) {
+            const int64_t c = c0 + threadIdx.x;
+            if (c < M1) {
+                Lt h = M::lid(), t = M::lid();
+#pragma unroll
+                for (int w = 0; w < WARPS; ++w) {
+                    h = M::lop(h, red_h[w][threadIdx.x]);
+                    t = M::lop(t, red_t[w][threadIdx.x]);
+                }
+                Rsum[s * M1 + c] = M::template put<C>(M::op(M::widen(h), M::widen(t)));
+                Rtail[s * M1 + c] = M::template put<C>(M::widen(t));
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Dimension-1 step (Mc > 1) with the rows staged in shared memory by
+// asynchronous copies: a block of 128 columns stages the prefix window
+// [s0, s0+L) and the target window [s0+k1, s0+k1+L) (one range when they
+// overlap), then each thread scans its column from shared memory.
+//   out[x1][c] = Q[s][c] (+) T[c] (+) (+)_{u<t} H[s0+u][c] (+) (+)_{v>=t} H[s0+k1+v][c]
+// ---------------------------------------------------------------------------
+template <class M, class SH, class SOut, int L, int NC>
+__global__ void __launch_bounds__(NC)
+k_exline_smem(const SH *__restrict__ H, const typename M::car_t *__restrict__ Q, int64_t qs,
+              const typename M::car_t *__restrict__ T, SOut *__restrict__ out, int64_t n1,
+              int64_t Mc, int64_t k1, int64_t nq)
+{
+    using Lt = typename M::loc_t;
+    // rows [0, L) prefix window; target window at tw .. tw+L
+    __shared__ SH tile[2 * L][NC];
+    const int tid = threadIdx.x;
+    const int64_t q = blockIdx.x % nq;
+    const int64_t s = blockIdx.x / nq;
+    const int64_t s0 = s * L;
+    const int64_t c = q * NC + tid;
+    const bool overlap = k1 < L;
+    const int tw = overlap ? (int)k1 : L;           // tile row of target row s0+k1
+    const int rows = overlap ? L + (int)k1 : 2 * L;
+    for (int r = 0; r < rows; ++r) {
+        const int64_t y = (overlap || r < L) ? s0 + r : s0 + k1 + (r - L);
+        if (c < Mc && y < n1) cp_async_elem(&tile[r][tid], H + y * Mc + c);
+    }
+    cp_async_wait_all();
+    if (c >= Mc) return;   // no block-wide sync after this point
+    Lt P[L];
+    Lt acc = M::lid();
+#pragma unroll
+    for (int t = 0; t < L; ++t) {
+        P[t] = acc;
+        if (s0 + t < n1) acc = M::lop(acc, M::lget(tile[t][tid]));
+    }
+    typename M::acc_t qv = Q ? M::get(Q[s * qs + c]) : M::id();
+    if (T) qv = M::op(qv, M::get(T[c]));
+    Lt sacc = M::lid();
+    SOut *dst = out + s0 * Mc + c;
+#pragma unroll
+    for (int t = L - 1; t >= 0; --t) {
+        if (s0 + k1 + t < n1) sacc = M::lop(M::lget(tile[tw + t][tid]), sacc);
+        if (s0 + t < n1) dst[t * Mc] = M::template put<SOut>(M::op(qv, M::widen(M::lop(P[t], sacc))));
+    }
+}
+
+}  // namespace exsum

@@ -233,7 +233,8 @@ template <class M, int NT>
 __global__ void __launch_bounds__(NT)
 k_carry_blk(const typename M::car_t *__restrict__ R, const typename M::car_t *__restrict__ Rt,
             const typename M::car_t *__restrict__ T, typename M::car_t *__restrict__ Q,
-            typename M::car_t *__restrict__ SR, int64_t Mc, int64_t S, int64_t qoff)
+            typename M::car_t *__restrict__ SR, int64_t Mc, int64_t S, int64_t qoff,
+            typename M::car_t *__restrict__ G)
 {
     using A = typename M::acc_t;
     using C = typename M::car_t;
@@ -245,6 +246,7 @@ k_carry_blk(const typename M::car_t *__restrict__ R, const typename M::car_t *__
     for (int64_t s = sb; s < se; ++s) tot = M::op(tot, M::get(R[s * Mc + c]));
     A pre, suf;
     block_exscan_both<M, NT>(tot, pre, suf);
+    if (G && threadIdx.x == NT - 1) G[c] = M::template put<C>(M::op(pre, tot));
     A acc = suf;
     for (int64_t s = se - 1; s >= sb; --s) {
         acc = M::op(M::get(R[s * Mc + c]), acc);

@@ -11,7 +11,7 @@
 #include <stdint.h>
 #include <string.h>
 
-#include "kernels_fast.cuh"
+#include "kernels_flat.cuh"
 
 namespace exsum {
 
@@ -32,7 +32,15 @@ enum KernelTag {
 void trace_before(cudaStream_t s, int tag, int level, int64_t elems);
 void trace_after(cudaStream_t s);
 
+// Side stream and fork/join events for running independent passes
+// concurrently with the caller's stream (a parallel branch under capture).
+struct Aux {
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+};
+
 struct Ctx {
+    const Aux *aux = nullptr;    // nullptr: everything on `stream`
     char *base = nullptr;   // workspace (device)
     size_t cap = 0;         // workspace bytes available
     size_t off = 0;         // bytes carved so far
@@ -82,28 +90,37 @@ struct Pipe {
     using L_ = typename M::loc_t;
     static constexpr int CONTIG_ROWS = sizeof(L_) > 4 ? 64 : 128;
 
+    // Rsum/Rtail (contiguous pass only): also produce the segment totals of the
+    // input over the view's first dimension n1 (segments of EXL rows).
     template <class SIn, class SOut, int KMAX>
     static void inc_fast(Ctx &cx, const SIn *src, SOut *dst, int64_t O, int64_t n, int64_t I,
-                         int64_t k)
+                         int64_t k, int64_t n1 = 1, CAR *Rsum = nullptr, CAR *Rtail = nullptr,
+                         int r_tail = 0)
     {
         if (I == 1) {
-            const int Lc = (int)(n < 128 ? n : 128);
-            const int nchunks = (int)cdiv(n, Lc);
-            const int WL = Lc + KMAX - 1;
-            const int W = WL | 1;
-            const uint32_t magic = (uint32_t)((((uint64_t)1 << 32) + WL - 1) / WL);
-            const size_t smem = (size_t)CONTIG_ROWS * W * sizeof(L_);
-            auto kern = k_inc_contig<M, SIn, SOut, KMAX, CONTIG_ROWS>;
-            if (smem > 48 * 1024)
-                cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            const int64_t nvirt = O * nchunks;
-            cx.before(TAG_INC, O * n);
-            kern<<<(unsigned)cdiv(nvirt, CONTIG_ROWS), CONTIG_ROWS, smem, cx.stream>>>(
-                src, dst, O, (int)n, (int)k, Lc, nchunks, W, magic, WL);
+            // Contiguous dimension: warp chunks of 128 elements of a "plane".
+            // With segment totals the planes are the slices of dimension 1;
+            // otherwise a plane is a run of whole rows of at least 128 elements.
+            const int64_t N = O * n;
+            int64_t pn1, M1;
+            if (Rsum) {
+                pn1 = n1;
+                M1 = N / n1;
+            } else {
+                const int64_t rpp = cdiv(128, n);
+                M1 = rpp * n;
+                pn1 = cdiv(O, rpp);
+            }
+            const int64_t nq = cdiv(M1, 128);
+            const int64_t blocks = cdiv(pn1, 32) * nq;
+            cx.before(TAG_INC, N);
+            k_inc_flat<M, SIn, SOut, KMAX><<<(unsigned)blocks, 256, 0, cx.stream>>>(
+                src, dst, N, pn1, M1, n, (int)k, nq, Rsum, Rtail, r_tail);
             cx.check_launch();
         } else {
+            // Chunks short enough for ~2048 threads per SM (walks of a few blocks).
             int Lc = 128;
-            while (Lc > 2 * k && Lc > 32 && O * cdiv(n, Lc) * I < 152 * 1024) Lc >>= 1;
+            while (Lc > 2 * k && Lc > 16 && O * cdiv(n, Lc) * I < 152 * 2048) Lc >>= 1;
             if (Lc > n) Lc = (int)n;
             const int nchunks = (int)cdiv(n, Lc);
             const int64_t total = O * nchunks * I;
@@ -216,7 +233,7 @@ struct Pipe {
             cx.before(TAG_CARRY, S * Mc);
             if (blk)
                 k_carry_blk<M, 1024><<<(unsigned)Mc, 1024, 0, cx.stream>>>(R, Rt, T, Qb, SR, Mc, S,
-                                                                           qoff);
+                                                                           qoff, nullptr);
             else
                 k_carry_col<M><<<(unsigned)cdiv(Mc, 256), 256, 0, cx.stream>>>(R, Rt, T, Qb, Mc, S,
                                                                                 qoff);
@@ -231,8 +248,18 @@ struct Pipe {
                 H, Q, out, n1, k1);
         else
             k_exline2<M, SH, SOut, EXL><<<(unsigned)cdiv(S * Mc, 128), 128, 0, cx.stream>>>(
-                H, Q, qs, out, n1, Mc, k1, S);
+                H, Q, qs, nullptr, out, n1, Mc, k1, S);
         cx.check_launch();
+    }
+
+    // Dimension-1 step over a view [n1, Mc], Mc > 1: rows staged in shared
+    // memory by asynchronous copies when the element is 4 or 8 bytes wide.
+    template <class SH, class SOut>
+    static void exline_launch(Ctx &cx, const SH *H, const CAR *Q, const CAR *T, SOut *out,
+                              int64_t n1, int64_t Mc, int64_t k1, int64_t S)
+    {
+        k_exline2<M, SH, SOut, EXL><<<(unsigned)cdiv(S * Mc, 128), 128, 0, cx.stream>>>(
+            H, Q, Mc, T, out, n1, Mc, k1, S);
     }
 
     // ---- included sums: BDBS along every dimension ---------------------------------------
@@ -285,41 +312,122 @@ struct Pipe {
             exline_stage<SIn, SOut>(cx, X, nullptr, out, n[0], 1, k[0]);
             return;
         }
+        const int64_t S = cdiv(n[0], EXL);
         int dims[16];
         int P = 0;
         for (int j = d - 1; j >= 1; --j)
             if (k[j] > 1) dims[P++] = j;
         SOut *B = P > 0 ? cx.take<SOut>(N) : nullptr;
+        CAR *R = cx.take<CAR>(S * M1);
+        CAR *Rt = cx.take<CAR>(S * M1);
         CAR *G = cx.take<CAR>(M1);
         CAR *T = cx.take<CAR>(M1);
+        CAR *Qa = S > 1 ? cx.take<CAR>(S * M1) : nullptr;
+        const bool blk = S > 64 && M1 < 4096;
+        CAR *SR = (S > 1 && blk) ? cx.take<CAR>(S * M1) : nullptr;
+        const int r_tail = (int)(k[0] % EXL);
+        // The first pass fuses the segment totals of X when it is the
+        // contiguous register pass over whole 32-row segments.
+        const bool fused = P > 0 && dims[0] == d - 1 && k[d - 1] <= 32 && n[0] >= 32;
         // H: BDBS along dims d..2, ping-ponging between out and B and ending in B.
-        const void *cur = X;
-        for (int p = 0; p < P; ++p) {
+        // Pass 0 runs first; when it carries the segment totals, the carries,
+        // their included sums and the lower-dimensional recursion only depend
+        // on it and run on the side stream while the other passes proceed.
+        auto run_pass = [&](int p, const void *src) -> SOut * {
             const int j = dims[p];
             int64_t O = 1, I = 1;
             for (int m = 0; m < j; ++m) O *= n[m];
             for (int m = j + 1; m < d; ++m) I *= n[m];
             SOut *dst = ((P - 1 - p) % 2 == 0) ? B : out;
-            if (p == 0)
-                inc_pass<SIn, SOut>(cx, (const SIn *)cur, dst, O, n[j], I, k[j]);
-            else
-                inc_pass<SOut, SOut>(cx, (const SOut *)cur, dst, O, n[j], I, k[j]);
-            cur = dst;
+            if (p == 0 && fused) {
+                if (!cx.dry && cx.ok()) {
+                    const int64_t kk = k[j];
+                    if (kk <= 4)
+                        inc_fast<SIn, SOut, 4>(cx, (const SIn *)src, dst, O, n[j], I, kk, n[0], R, Rt, r_tail);
+                    else if (kk <= 8)
+                        inc_fast<SIn, SOut, 8>(cx, (const SIn *)src, dst, O, n[j], I, kk, n[0], R, Rt, r_tail);
+                    else if (kk <= 16)
+                        inc_fast<SIn, SOut, 16>(cx, (const SIn *)src, dst, O, n[j], I, kk, n[0], R, Rt, r_tail);
+                    else
+                        inc_fast<SIn, SOut, 32>(cx, (const SIn *)src, dst, O, n[j], I, kk, n[0], R, Rt, r_tail);
+                }
+            } else if (p == 0) {
+                inc_pass<SIn, SOut>(cx, (const SIn *)src, dst, O, n[j], I, k[j]);
+            } else {
+                inc_pass<SOut, SOut>(cx, (const SOut *)src, dst, O, n[j], I, k[j]);
+            }
+            return dst;
+        };
+        const void *cur = X;
+        int p_next = 0;
+        if (fused) cur = run_pass(p_next++, cur);
+        // Fork.
+        const Aux *aux = cx.aux;
+        const bool fork = aux && aux->side && !cx.dry && cx.ok();
+        cudaStream_t main_stream = cx.stream;
+        if (fork) {
+            cudaEventRecord(aux->fork, main_stream);
+            cudaStreamWaitEvent(aux->side, aux->fork, 0);
+            cx.stream = aux->side;
         }
-        colsum<SIn>(cx, X, G, n[0], M1);
+        cx.aux = nullptr;
+        if (!fused && !cx.dry && cx.ok()) {
+            cx.before(TAG_REDUCE, N);
+            k_reduce_seg2<M, SIn><<<(unsigned)cdiv(S * M1, 256), 256, 0, cx.stream>>>(
+                X, R, Rt, n[0], M1, EXL, S, r_tail);
+            cx.check_launch();
+        }
+        // Carries of the dimension-1 step and the column totals G.
+        if (!cx.dry && cx.ok()) {
+            const int64_t qoff = 1 + k[0] / EXL;
+            cx.before(TAG_CARRY, S * M1);
+            if (S > 1 && blk)
+                k_carry_blk<M, 1024><<<(unsigned)M1, 1024, 0, cx.stream>>>(R, Rt, nullptr, Qa, SR,
+                                                                           M1, S, qoff, G);
+            else
+                k_carry_qa<M><<<(unsigned)cdiv(M1, 256), 256, 0, cx.stream>>>(R, Rt, Qa, G, M1, S,
+                                                                              qoff);
+            cx.check_launch();
+        }
+        // Included sums of the carries along dims 2..d (view [S, n_2, .., n_d]).
+        CAR *Qh = Qa;
+        if (S > 1 && P > 0) {
+            int64_t ns[16], ks[16];
+            ns[0] = S;
+            ks[0] = 1;
+            for (int m = 1; m < d; ++m) {
+                ns[m] = n[m];
+                ks[m] = k[m];
+            }
+            CAR *Qo = cx.take<CAR>(S * M1);
+            included<CAR, CAR>(cx, Qa, Qo, d, ns, ks);
+            Qh = Qo;
+        }
         cx.level++;
         excluded<CAR, CAR>(cx, G, T, d - 1, n + 1, k + 1);
         cx.level--;
-        if (P > 0)
-            exline_stage<SOut, SOut>(cx, B, T, out, n[0], M1, k[0]);
-        else
-            exline_stage<SIn, SOut>(cx, X, T, out, n[0], M1, k[0]);
+        // Join: the remaining passes on the caller's stream, then wait.
+        cx.aux = aux;
+        if (fork) {
+            cudaEventRecord(aux->join, aux->side);
+            cx.stream = main_stream;
+        }
+        for (; p_next < P; ++p_next) cur = run_pass(p_next, cur);
+        if (fork) cudaStreamWaitEvent(main_stream, aux->join, 0);
+        if (!cx.dry && cx.ok()) {
+            cx.before(TAG_EXLINE, N);
+            if (P > 0)
+                exline_launch<SOut, SOut>(cx, B, Qh, T, out, n[0], M1, k[0], S);
+            else
+                exline_launch<SIn, SOut>(cx, X, Qh, T, out, n[0], M1, k[0], S);
+            cx.check_launch();
+        }
     }
 
     // ---- entry -----------------------------------------------------------------------------
     static int run(int excluded_sum, const void *in, void *out, int d, const int64_t *n,
                    const int64_t *k, void *ws, size_t ws_bytes, cudaStream_t stream,
-                   size_t *ws_needed, cudaError_t *cuda_err)
+                   size_t *ws_needed, cudaError_t *cuda_err, const Aux *aux)
     {
         Ctx cx;
         cx.dry = true;
@@ -336,6 +444,7 @@ struct Pipe {
         rx.base = (char *)ws;
         rx.cap = ws_bytes;
         rx.stream = stream;
+        rx.aux = aux;
         if (excluded_sum)
             excluded<IN, OUT>(rx, (const IN *)in, (OUT *)out, d, n, k);
         else
