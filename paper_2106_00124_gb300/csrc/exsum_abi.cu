@@ -129,8 +129,11 @@ static const exsum::Aux *aux_for(void *stream)
     }
     exsum::Aux a;
     if (cudaStreamCreateWithFlags(&a.side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&a.side2, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&a.fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&a.join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&a.join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&a.fork2, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&a.join2, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         a = exsum::Aux();
     }

@@ -109,7 +109,7 @@ k_inc_flat(const SIn *__restrict__ in, SOut *__restrict__ out, int64_t N, int64_
     using Lt = typename M::loc_t;
     using C = typename M::car_t;
     constexpr int SEG = 32, WARPS = 8, CH = 128, HALO = 32;
-    __shared__ Lt buf[WARPS][CH + HALO];
+    __shared__ __align__(16) Lt buf[WARPS][CH + HALO];
     __shared__ Lt red_h[WARPS][CH], red_t[WARPS][CH];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t q = blockIdx.x % nq;          // chunk position in the plane
@@ -134,8 +134,15 @@ k_inc_flat(const SIn *__restrict__ in, SOut *__restrict__ out, int64_t N, int64_
         const SIn *src = in + base + 4 * lane;
         const bool vin = valid == 4 && (((uintptr_t)src) & (4 * sizeof(SIn) - 1)) == 0;
         load4<M>(src, vin, valid, v);
+        // 16-byte (or 2 x 16-byte) shared stores: no bank conflicts
+        if constexpr (sizeof(Lt) == 4) {
+            float4 w;
+            memcpy(&w, v, 16);
+            *reinterpret_cast<float4 *>(sb + 4 * lane) = w;
+        } else {
 #pragma unroll
-        for (int i = 0; i < 4; ++i) sb[4 * lane + i] = v[i];
+            for (int i = 0; i < 4; ++i) sb[4 * lane + i] = v[i];
+        }
         sb[CH + lane] = (CH + lane < lim_c) ? M::lget(in[base + CH + lane]) : M::lid();
         __syncwarp();
         if (sums) {
@@ -147,9 +154,26 @@ k_inc_flat(const SIn *__restrict__ in, SOut *__restrict__ out, int64_t N, int64_
                     ts[i] = M::lop(ts[i], v[i]);
             }
         }
-        Lt st[4 + KMAX - 1];
+        // The lane's strip: its own 4 values, then KMAX-1 values of the lanes
+        // after it (read as 16-byte vectors from 16-byte-aligned offsets).
+        Lt st[4 + KMAX + 3];
 #pragma unroll
-        for (int j = 0; j < 4 + KMAX - 1; ++j) st[j] = (4 * lane + j < CH + HALO) ? sb[4 * lane + j] : M::lid();
+        for (int i = 0; i < 4; ++i) st[i] = v[i];
+        if constexpr (sizeof(Lt) == 4) {
+#pragma unroll
+            for (int j = 4; j < 4 + KMAX; j += 4) {
+                if (4 * lane + j < CH + HALO) {
+                    const float4 w = *reinterpret_cast<const float4 *>(sb + 4 * lane + j);
+                    memcpy(st + j, &w, 16);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) st[j + i] = M::lid();
+                }
+            }
+        } else {
+#pragma unroll
+            for (int j = 4; j < 4 + KMAX; ++j) st[j] = (4 * lane + j < CH + HALO) ? sb[4 * lane + j] : M::lid();
+        }
         __syncwarp();
         Lt o[4];
 #pragma unroll

@@ -35,8 +35,8 @@ void trace_after(cudaStream_t s);
 // Side stream and fork/join events for running independent passes
 // concurrently with the caller's stream (a parallel branch under capture).
 struct Aux {
-    cudaStream_t side = nullptr;
-    cudaEvent_t fork = nullptr, join = nullptr;
+    cudaStream_t side = nullptr, side2 = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr, fork2 = nullptr, join2 = nullptr;
 };
 
 struct Ctx {
@@ -389,6 +389,13 @@ struct Pipe {
                                                                               qoff);
             cx.check_launch();
         }
+        // Second branch: the lower-dimensional recursion only needs G; it runs
+        // on side2 while the carries' included sums run on side.
+        const bool fork2 = fork && aux->side2;
+        if (fork2) {
+            cudaEventRecord(aux->fork2, cx.stream);
+            cudaStreamWaitEvent(aux->side2, aux->fork2, 0);
+        }
         // Included sums of the carries along dims 2..d (view [S, n_2, .., n_d]).
         CAR *Qh = Qa;
         if (S > 1 && P > 0) {
@@ -403,6 +410,7 @@ struct Pipe {
             included<CAR, CAR>(cx, Qa, Qo, d, ns, ks);
             Qh = Qo;
         }
+        if (fork2) cx.stream = aux->side2;
         cx.level++;
         excluded<CAR, CAR>(cx, G, T, d - 1, n + 1, k + 1);
         cx.level--;
@@ -410,10 +418,12 @@ struct Pipe {
         cx.aux = aux;
         if (fork) {
             cudaEventRecord(aux->join, aux->side);
+            if (fork2) cudaEventRecord(aux->join2, aux->side2);
             cx.stream = main_stream;
         }
         for (; p_next < P; ++p_next) cur = run_pass(p_next, cur);
         if (fork) cudaStreamWaitEvent(main_stream, aux->join, 0);
+        if (fork2) cudaStreamWaitEvent(main_stream, aux->join2, 0);
         if (!cx.dry && cx.ok()) {
             cx.before(TAG_EXLINE, N);
             if (P > 0)
