@@ -161,6 +161,105 @@ int exsum_excluded_noalloc(const void *in, void *out, int d, const int64_t *shap
  * device first).  Returns 0 or EXSUM_ECUDA. */
 int exsum_release_cached_workspace(void);
 
+/* ---------------------------------------------------------------------------
+ * Batches of uneven tensors.  Not in the paper; it batches many independent
+ * excluded sums (Sec. 5) so that they fill the GPU together.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    const void *in;                  /* DEVICE input (host for EXSUM_SERVE_HOST requests) */
+    void *out;                       /* DEVICE output (host for EXSUM_SERVE_HOST requests) */
+    int d;                           /* dimensions, 1..EXSUM_MAX_DIMS */
+    int op;                          /* exsum_op */
+    int dtype;                       /* exsum_dtype of `in` */
+    int64_t shape[EXSUM_MAX_DIMS];   /* first d entries used */
+    int64_t k[EXSUM_MAX_DIMS];       /* first d entries used */
+} exsum_desc;
+
+typedef struct exsum_batch exsum_batch;
+
+/*
+ * Plans the excluded sums of `count` tensors as ONE CUDA graph.  Every
+ * descriptor is validated as for exsum_excluded (EXSUM_EINVAL otherwise).
+ * The tensors are assigned to `lanes` concurrent streams -- longest
+ * processing time first (order 0) or round-robin by size (order 1) -- each
+ * lane with one workspace sized for its largest tensor (allocated here with
+ * cudaMalloc), and the whole batch is captured into a graph bound to the
+ * descriptors' pointers.  lanes <= 0 autotunes: each candidate schedule (1..32
+ * lanes, both orders) is captured and its replays timed on the device
+ * (inputs are read and outputs written during tuning), and the fastest is
+ * kept; the choice is remembered per batch signature (shapes, boxes, ops,
+ * dtypes) for the process and, if the environment variable EXSUM_TUNE_CACHE
+ * names a file, appended there and read back by later processes.  `stream`
+ * must not be capturing (EXSUM_EBUSY).  On success *plan owns the graph and
+ * the lane workspaces until exsum_batch_destroy.
+ */
+int exsum_batch_create(const exsum_desc *descs, int count, int lanes, void *stream,
+                       exsum_batch **plan);
+
+/* Launches the planned batch on `stream` (one cudaGraphLaunch). */
+int exsum_batch_launch(exsum_batch *plan, void *stream);
+
+/* Schedule of a plan: lanes, order, total lane workspace bytes, kernels per launch. */
+int exsum_batch_info(const exsum_batch *plan, int *lanes, int *order, size_t *workspace_bytes,
+                     int64_t *kernels);
+
+/* Waits for the device, then frees the plan's graph and workspaces. */
+void exsum_batch_destroy(exsum_batch *plan);
+
+/* ---------------------------------------------------------------------------
+ * Request server (continuous batching).  Not in the paper.
+ * ------------------------------------------------------------------------- */
+typedef struct exsum_server exsum_server;
+
+/* In/out of a submitted request are HOST pointers: the server stages them
+ * through its device memory (copy in, compute, copy out). */
+#define EXSUM_SERVE_HOST 1
+
+/*
+ * Starts a server on the current device: one device arena of
+ * `mem_budget_bytes` (allocated here, once) for the requests' workspaces and
+ * staging buffers, `max_slots` CUDA streams (1..256) on which admitted
+ * requests run concurrently, and a host worker thread.  Returns NULL on
+ * invalid arguments or if the arena or streams cannot be created.
+ */
+exsum_server *exsum_server_create(size_t mem_budget_bytes, int max_slots);
+
+/*
+ * Queues one excluded sum (box-complement, as exsum_excluded).  Requests are
+ * admitted in arrival order as soon as a slot is free and the request's
+ * memory (workspace, plus input and output for EXSUM_SERVE_HOST) fits in the
+ * free part of the budget; requests arriving while others run are admitted
+ * as memory and slots free up, and run concurrently with them.  Device
+ * pointers must stay valid, and host buffers untouched, until the request
+ * completes.  Returns EXSUM_EINVAL for a malformed descriptor, EXSUM_ENOMEM
+ * for a request larger than the whole budget, EXSUM_EBUSY after shutdown
+ * began; otherwise *ticket identifies the request.
+ */
+int exsum_server_submit(exsum_server *srv, const exsum_desc *desc, int flags, uint64_t *ticket);
+
+/*
+ * Waits at most timeout_ns for a request: its status once complete,
+ * EXSUM_ETIMEDOUT if still queued or running at the deadline (never blocks
+ * longer), EXSUM_EINVAL for an unknown ticket.
+ */
+int exsum_server_wait(exsum_server *srv, uint64_t ticket, int64_t timeout_ns);
+
+/* Host steady-clock times (ns) of a completed request: submission, admission
+ * (work queued on its slot) and completion (signalled from its stream). */
+int exsum_server_ticket_times(exsum_server *srv, uint64_t ticket, int64_t *submit_ns,
+                              int64_t *start_ns, int64_t *done_ns);
+
+/* Forgets a completed request (its ticket becomes unknown); EXSUM_EBUSY if
+ * it has not completed. */
+int exsum_server_release(exsum_server *srv, uint64_t ticket);
+
+/* Requests completed so far, or -1 for a NULL server. */
+int64_t exsum_server_completed(exsum_server *srv);
+
+/* Stops admitting new requests, finishes every queued and running one,
+ * then frees the server. */
+void exsum_server_destroy(exsum_server *srv);
+
 /*
  * Launch trace.  The paper reports time per element (Sec. 6); this breaks a
  * call's device time down by pass.  While enabled, every kernel the library

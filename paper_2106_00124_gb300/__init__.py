@@ -43,6 +43,30 @@ class ExsumError(RuntimeError):
 
 _lib = None
 
+
+class exsum_desc(ctypes.Structure):
+    """C struct exsum_desc: one tensor of a batch or one served request."""
+    _fields_ = [("in_", ctypes.c_void_p), ("out", ctypes.c_void_p), ("d", ctypes.c_int),
+                ("op", ctypes.c_int), ("dtype", ctypes.c_int),
+                ("shape", ctypes.c_int64 * MAX_DIMS), ("k", ctypes.c_int64 * MAX_DIMS)]
+
+
+def make_desc(in_ptr, out_ptr, shape, k, op, dtype):
+    """An exsum_desc for device (or, for served host requests, host) pointers."""
+    dsc = exsum_desc()
+    dsc.in_ = in_ptr
+    dsc.out = out_ptr
+    dsc.d = len(shape)
+    dsc.op = int(op)
+    dsc.dtype = int(dtype)
+    for i, (n, kk) in enumerate(zip(shape, k)):
+        dsc.shape[i] = int(n)
+        dsc.k[i] = int(kk)
+    return dsc
+
+
+SERVE_HOST = 1
+
 _P = ctypes.c_void_p
 _I64P = ctypes.POINTER(ctypes.c_int64)
 _SIG = {
@@ -70,6 +94,23 @@ _SIG = {
                              ctypes.c_int, ctypes.c_int], ctypes.c_int),
     "exsum_kernel_name": ([ctypes.c_int], ctypes.c_char_p),
     "exsum_launch_count": ([], ctypes.c_int64),
+    "exsum_batch_create": ([ctypes.POINTER(exsum_desc), ctypes.c_int, ctypes.c_int, _P,
+                            ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
+    "exsum_batch_launch": ([_P, _P], ctypes.c_int),
+    "exsum_batch_info": ([_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                          ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_int64)],
+                         ctypes.c_int),
+    "exsum_batch_destroy": ([_P], None),
+    "exsum_server_create": ([ctypes.c_size_t, ctypes.c_int], _P),
+    "exsum_server_submit": ([_P, ctypes.POINTER(exsum_desc), ctypes.c_int,
+                             ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
+    "exsum_server_wait": ([_P, ctypes.c_uint64, ctypes.c_int64], ctypes.c_int),
+    "exsum_server_ticket_times": ([_P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int64),
+                                   ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)],
+                                  ctypes.c_int),
+    "exsum_server_release": ([_P, ctypes.c_uint64], ctypes.c_int),
+    "exsum_server_completed": ([_P], ctypes.c_int64),
+    "exsum_server_destroy": ([_P], None),
 }
 
 
@@ -188,6 +229,66 @@ def exsum_kernel_name(tag):
 
 def exsum_launch_count():
     return int(_load().exsum_launch_count())
+
+
+def exsum_batch_create(descs, lanes=0, stream=0):
+    """Plans a batch (a sequence of exsum_desc); returns (status, plan handle)."""
+    arr = (exsum_desc * len(descs))(*descs)
+    plan = ctypes.c_void_p(0)
+    rc = _load().exsum_batch_create(arr, len(descs), int(lanes), stream or None, ctypes.byref(plan))
+    return rc, plan.value
+
+
+def exsum_batch_launch(plan, stream=0):
+    return _load().exsum_batch_launch(plan, stream or None)
+
+
+def exsum_batch_info(plan):
+    """(status, lanes, order, workspace_bytes, kernels_per_launch)."""
+    lanes, order, ws, ker = ctypes.c_int(), ctypes.c_int(), ctypes.c_size_t(), ctypes.c_int64()
+    rc = _load().exsum_batch_info(plan, ctypes.byref(lanes), ctypes.byref(order), ctypes.byref(ws),
+                                  ctypes.byref(ker))
+    return rc, lanes.value, order.value, ws.value, ker.value
+
+
+def exsum_batch_destroy(plan):
+    _load().exsum_batch_destroy(plan)
+
+
+def exsum_server_create(mem_budget_bytes, max_slots):
+    """Returns a server handle, or None."""
+    return _load().exsum_server_create(int(mem_budget_bytes), int(max_slots))
+
+
+def exsum_server_submit(server, desc, flags=0):
+    """Returns (status, ticket)."""
+    t = ctypes.c_uint64(0)
+    rc = _load().exsum_server_submit(server, ctypes.byref(desc), int(flags), ctypes.byref(t))
+    return rc, t.value
+
+
+def exsum_server_wait(server, ticket, timeout_ns):
+    return _load().exsum_server_wait(server, int(ticket), int(timeout_ns))
+
+
+def exsum_server_ticket_times(server, ticket):
+    """Returns (status, submit_ns, start_ns, done_ns)."""
+    a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    rc = _load().exsum_server_ticket_times(server, int(ticket), ctypes.byref(a), ctypes.byref(b),
+                                           ctypes.byref(c))
+    return rc, a.value, b.value, c.value
+
+
+def exsum_server_release(server, ticket):
+    return _load().exsum_server_release(server, int(ticket))
+
+
+def exsum_server_completed(server):
+    return int(_load().exsum_server_completed(server))
+
+
+def exsum_server_destroy(server):
+    _load().exsum_server_destroy(server)
 
 
 # ---- torch conveniences ------------------------------------------------------------------------

@@ -141,6 +141,12 @@ static const exsum::Aux *aux_for(void *stream)
     return a.side ? &g_aux[key] : nullptr;
 }
 
+namespace exsum {
+// Creates (outside any capture) the side streams of a caller stream, so that
+// later calls on that stream fork even while it is being captured.
+const void *aux_prepare(void *stream) { return aux_for(stream); }
+}  // namespace exsum
+
 static int run(int excluded, const void *in, void *out, int d, const int64_t *shape,
                const int64_t *k, int op, int dtype, void *ws, size_t ws_bytes, void *stream,
                size_t *need, bool allow_fork = true)
