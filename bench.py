@@ -52,6 +52,11 @@ def parse_args(argv=None):
     p.add_argument("--workload", default=DEFAULT_WORKLOAD)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--mode", choices=["single", "batched", "served"], default="single",
+                   help="single: the default step; batched: 512 uneven tensors as one graph "
+                        "launch vs plain per-tensor launches; served: a Poisson request stream "
+                        "at three offered loads (p50/p99) vs one-at-a-time plain launches")
+    p.add_argument("--requests", type=int, default=20000)
     p.add_argument("--profile-once", action="store_true",
                    help="run the workload's excluded sum twice without graphs or timing "
                         "(a small, self-ending command for ncu) and exit")
@@ -484,8 +489,179 @@ def run_profile_once(args):
     print(json.dumps({"profile_once": args.workload, "launches": ex.exsum_launch_count()}))
 
 
+def _seeded_device_tensors(shapes, seed, dtype):
+    """Seeded synthetic tensors generated on the device (uniform [-1, 1) fp32,
+    or integers in [-1000, 1000] for int64)."""
+    import torch
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(seed)
+    out = []
+    for shape in shapes:
+        if dtype == "f32":
+            out.append(torch.rand(shape, generator=gen, device="cuda") * 2 - 1)
+        else:
+            out.append(torch.randint(-1000, 1001, shape, generator=gen, device="cuda",
+                                     dtype=torch.int64))
+    return out
+
+
+def run_batched(args):
+    """512 uneven tensors: d in {2, 3}, sides uniform in [32, 512] (at most 2^24
+    elements), k_i uniform in [2, 32], fp32 uniform [-1, 1), +."""
+    import numpy as np
+    import torch
+
+    import paper_2106_00124_gb300 as ex
+    from paper_2106_00124_gb300 import synth
+    torch.cuda.set_device(0)
+    spec = synth.batched_shapes(512, seed=11)
+    xs = _seeded_device_tensors([s_ for s_, _ in spec], 11, "f32")
+    outs = [torch.empty_like(x) for x in xs]
+    descs = [ex.make_desc(x.data_ptr(), o.data_ptr(), sh, k, ex.OP_ADD, ex.F32)
+             for x, o, (sh, k) in zip(xs, outs, spec)]
+    total = sum(int(np.prod(sh)) for sh, _ in spec)
+    stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    rc, plan = ex.exsum_batch_create(descs, lanes=0, stream=stream.cuda_stream)
+    tune_s = time.perf_counter() - t0
+    assert rc == 0, ex.strerror(rc)
+    _, lanes, order, wsb, kernels = ex.exsum_batch_info(plan)
+    for _ in range(max(1, args.warmup)):
+        ex.exsum_batch_launch(plan, stream.cuda_stream)
+    torch.cuda.synchronize()
+    steps = max(3, min(args.steps, 20))
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        ex.exsum_batch_launch(plan, stream.cuda_stream)
+    b.record(stream)
+    torch.cuda.synchronize()
+    batch_ms = a.elapsed_time(b) / steps
+    # plain per-tensor launches on one stream (no graph, no concurrency)
+    need = max(ex.exsum_workspace_bytes(len(sh), sh, k, ex.OP_ADD, ex.F32, 1)[0] for sh, k in spec)
+    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    sp = stream.cuda_stream
+
+    def plain():
+        for x, o, (sh, k) in zip(xs, outs, spec):
+            ex.exsum_excluded_ws(x.data_ptr(), o.data_ptr(), len(sh), sh, k, ex.OP_ADD, ex.F32,
+                                 ws.data_ptr(), need, sp)
+    plain()
+    torch.cuda.synchronize()
+    ref = [o.clone() for o in outs[:8]]
+    plain_steps = 3
+    a.record(stream)
+    for _ in range(plain_steps):
+        plain()
+    b.record(stream)
+    torch.cuda.synchronize()
+    plain_ms = a.elapsed_time(b) / plain_steps
+    ex.exsum_batch_launch(plan, sp)
+    torch.cuda.synchronize()
+    same = all(torch.equal(r_, o) for r_, o in zip(ref, outs[:8]))
+    ex.exsum_batch_destroy(plan)
+    print(json.dumps({
+        "metric": "batched excluded-sum Gelem/s", "unit": "Gelem/s",
+        "value": round(total / (batch_ms * 1e-3) / 1e9, 3),
+        "plain_value": round(total / (plain_ms * 1e-3) / 1e9, 3),
+        "speedup_vs_plain": round(plain_ms / batch_ms, 3), "ms_per_batch": round(batch_ms, 3),
+        "plain_ms_per_batch": round(plain_ms, 3), "tensors": len(spec), "elements": total,
+        "schedule": {"lanes": lanes, "order": ["lpt", "round_robin"][order],
+                     "kernels_per_launch": kernels, "lane_workspace_bytes": wsb,
+                     "autotune_s": round(tune_s, 2)},
+        "identical_to_plain": same, "dtype": "f32", "data": "synthetic (seeded, on device)",
+        "config": {"workload": "batched_512_uneven_d2d3_f32_add",
+                   "sides": [32, 512], "k": [2, 32], "cap": 1 << 24}}), flush=True)
+
+
+def run_served(args):
+    """A Poisson stream of excluded-sum requests (shapes and boxes as in the
+    batched workload, 90% fp32 +, 10% int64 max) served with continuous
+    batching at three offered loads, against one-at-a-time plain launches."""
+    import numpy as np
+    import torch
+
+    import paper_2106_00124_gb300 as ex
+    from paper_2106_00124_gb300 import synth
+    torch.cuda.set_device(0)
+    f_spec = synth.batched_shapes(48, seed=12)
+    i_spec = synth.batched_shapes(8, seed=13)
+    fx = _seeded_device_tensors([s_ for s_, _ in f_spec], 12, "f32")
+    ix = _seeded_device_tensors([s_ for s_, _ in i_spec], 13, "i64")
+    fo = [torch.empty_like(x) for x in fx]
+    io = [torch.empty_like(x) for x in ix]
+    rng = np.random.default_rng(14)
+    nreq = args.requests
+    kinds = rng.random(nreq) < 0.1
+    picks = [int(rng.integers(0, len(i_spec) if kd else len(f_spec))) for kd in kinds]
+    descs, sizes = [], []
+    for kd, j in zip(kinds, picks):
+        if kd:
+            sh, k = i_spec[j]
+            descs.append(ex.make_desc(ix[j].data_ptr(), io[j].data_ptr(), sh, k, ex.OP_MAX, ex.I64))
+        else:
+            sh, k = f_spec[j]
+            descs.append(ex.make_desc(fx[j].data_ptr(), fo[j].data_ptr(), sh, k, ex.OP_ADD, ex.F32))
+        sizes.append(int(np.prod(sh)))
+    budget = 40 << 30
+
+    def serve(slots, rate, n):
+        srv = ex.exsum_server_create(budget, slots)
+        assert srv
+        start = ex.exsum_server_now_ns() + 200_000_000
+        if rate is None:
+            arrivals = np.full(n, start, dtype=np.int64)
+        else:
+            gaps = rng.exponential(1e9 / rate, size=n)
+            arrivals = (start + np.cumsum(gaps)).astype(np.int64)
+        tickets = []
+        for i in range(n):
+            rc, t = ex.exsum_server_submit_at(srv, descs[i], 0, int(arrivals[i]))
+            assert rc == 0
+            tickets.append(t)
+        for t in tickets:
+            rc = ex.exsum_server_wait(srv, t, 60 * 10 ** 9)
+            if rc != 0:
+                raise RuntimeError("served request %d: %s" % (t, ex.strerror(rc)))
+        lat, first, last = [], None, 0
+        for t in tickets:
+            _, sub, st_, done = ex.exsum_server_ticket_times(srv, t)
+            lat.append((done - sub) / 1e6)
+            first = sub if first is None else min(first, sub)
+            last = max(last, done)
+        ex.exsum_server_destroy(srv)
+        span = (last - first) / 1e9
+        el = sum(sizes[:n])
+        return {"p50_ms": round(float(np.percentile(lat, 50)), 3),
+                "p99_ms": round(float(np.percentile(lat, 99)), 3),
+                "throughput_req_s": round(n / span, 1), "gelem_s": round(el / span / 1e9, 3)}
+
+    slots = 8
+    sat = serve(slots, None, min(nreq, 4000))          # saturated: everything arrives at once
+    sat_rate = sat["throughput_req_s"]
+    loads = {}
+    for f in (0.5, 0.8, 1.0):
+        loads[str(f)] = {"offered_req_s": round(f * sat_rate, 1),
+                         "served": serve(slots, f * sat_rate, nreq),
+                         "plain": serve(1, f * sat_rate, nreq)}
+    print(json.dumps({
+        "metric": "served excluded-sum p50/p99 latency and throughput", "unit": "ms / req/s",
+        "requests_per_load": nreq, "slots": slots, "budget_bytes": budget,
+        "saturated": sat, "loads": loads, "dtype": "f32 (+ int64 max)",
+        "data": "synthetic (seeded, on device)",
+        "config": {"workload": "served_poisson_uneven_d2d3_f32add_i64max",
+                   "plain": "the same arrivals served one request at a time (1 slot)"}}),
+        flush=True)
+
+
 def main(argv=None):
     args = parse_args(argv)
+    if args.mode == "batched":
+        run_batched(args)
+        return
+    if args.mode == "served":
+        run_served(args)
+        return
     if args.profile_once:
         run_profile_once(args)
         return

@@ -238,14 +238,28 @@ exsum_server *exsum_server_create(size_t mem_budget_bytes, int max_slots);
 int exsum_server_submit(exsum_server *srv, const exsum_desc *desc, int flags, uint64_t *ticket);
 
 /*
+ * As exsum_server_submit, for a request that arrives at `arrival_ns` on the
+ * server's clock (exsum_server_now_ns): it is not admitted before then, and
+ * its latency is measured from then.  Requests must be submitted in order of
+ * arrival (they are admitted first come, first served).  Lets a load
+ * generator hand the server a whole arrival schedule ahead of time.
+ */
+int exsum_server_submit_at(exsum_server *srv, const exsum_desc *desc, int flags,
+                           int64_t arrival_ns, uint64_t *ticket);
+
+/* The server's clock: host steady clock in nanoseconds. */
+int64_t exsum_server_now_ns(void);
+
+/*
  * Waits at most timeout_ns for a request: its status once complete,
  * EXSUM_ETIMEDOUT if still queued or running at the deadline (never blocks
  * longer), EXSUM_EINVAL for an unknown ticket.
  */
 int exsum_server_wait(exsum_server *srv, uint64_t ticket, int64_t timeout_ns);
 
-/* Host steady-clock times (ns) of a completed request: submission, admission
- * (work queued on its slot) and completion (signalled from its stream). */
+/* Server-clock times (ns) of a completed request: arrival (submission, or
+ * the arrival time given to exsum_server_submit_at), admission (work queued
+ * on its slot) and completion (signalled from its stream). */
 int exsum_server_ticket_times(exsum_server *srv, uint64_t ticket, int64_t *submit_ns,
                               int64_t *start_ns, int64_t *done_ns);
 

@@ -104,6 +104,9 @@ _SIG = {
     "exsum_server_create": ([ctypes.c_size_t, ctypes.c_int], _P),
     "exsum_server_submit": ([_P, ctypes.POINTER(exsum_desc), ctypes.c_int,
                              ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
+    "exsum_server_submit_at": ([_P, ctypes.POINTER(exsum_desc), ctypes.c_int, ctypes.c_int64,
+                                ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
+    "exsum_server_now_ns": ([], ctypes.c_int64),
     "exsum_server_wait": ([_P, ctypes.c_uint64, ctypes.c_int64], ctypes.c_int),
     "exsum_server_ticket_times": ([_P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int64),
                                    ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)],
@@ -265,6 +268,18 @@ def exsum_server_submit(server, desc, flags=0):
     t = ctypes.c_uint64(0)
     rc = _load().exsum_server_submit(server, ctypes.byref(desc), int(flags), ctypes.byref(t))
     return rc, t.value
+
+
+def exsum_server_submit_at(server, desc, flags, arrival_ns):
+    """Returns (status, ticket); the request is not admitted before arrival_ns."""
+    t = ctypes.c_uint64(0)
+    rc = _load().exsum_server_submit_at(server, ctypes.byref(desc), int(flags), int(arrival_ns),
+                                        ctypes.byref(t))
+    return rc, t.value
+
+
+def exsum_server_now_ns():
+    return int(_load().exsum_server_now_ns())
 
 
 def exsum_server_wait(server, ticket, timeout_ns):

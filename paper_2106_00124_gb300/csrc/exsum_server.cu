@@ -97,6 +97,7 @@ struct Request {
     int status = EXSUM_OK;
     bool done = false;
     int64_t t_submit = 0, t_start = 0, t_done = 0;
+    int64_t not_before = 0;          // arrival time: not admitted earlier
 };
 
 }  // namespace
@@ -146,7 +147,7 @@ void CUDART_CB on_complete(void *data)
     delete c;
 }
 
-// Enqueues an admitted request on its slot (called with the lock held).
+// Enqueues an admitted request on its slot (called without the lock).
 int launch(exsum_server *srv, Request &r)
 {
     cudaStream_t s = srv->slots[r.slot];
@@ -182,9 +183,17 @@ void worker_main(exsum_server *srv)
     cudaSetDevice(srv->device);
     std::unique_lock<std::mutex> lock(srv->mu);
     while (true) {
-        // Admit in arrival order while a slot is free and the head fits.
+        // Admit in arrival order while a slot is free and the head fits.  The
+        // lock is held only for the bookkeeping: CUDA calls are made without
+        // it, because the completion callback running on CUDA's own thread
+        // takes it.
+        int64_t wake_at = 0;
         while (!srv->pending.empty()) {
-            Request &r = srv->reqs[srv->pending.front()];
+            Request &head = srv->reqs[srv->pending.front()];
+            if (head.not_before > now_ns()) {
+                wake_at = head.not_before;
+                break;
+            }
             int slot = -1;
             for (size_t i = 0; i < srv->slots.size(); ++i)
                 if (!srv->slot_busy[i]) {
@@ -193,34 +202,48 @@ void worker_main(exsum_server *srv)
                 }
             if (slot < 0) break;
             size_t off = 0;
-            if (!srv->arena.alloc(r.need, &off)) break;
+            if (!srv->arena.alloc(head.need, &off)) break;
             srv->pending.pop_front();
-            r.off = off;
-            r.slot = slot;
+            head.off = off;
+            head.slot = slot;
+            head.t_start = now_ns();
             srv->slot_busy[slot] = 1;
-            r.t_start = now_ns();
+            Request r = head;   // a copy: the map may change while unlocked
+            lock.unlock();
             const int rc = launch(srv, r);
+            int rc2 = EXSUM_OK;
             if (rc) {
-                // Whatever was queued before the failure may still run: let the
-                // stream itself release the request's memory and slot once it
-                // drains.  The worker never synchronises while holding the lock
-                // (the completion callback takes it).
+                // Whatever was queued before the failure may still run: let
+                // the stream release the request's memory and slot once it
+                // drains.
                 cudaGetLastError();
-                r.status = rc;
                 Completion *c = new Completion{srv, r.ticket};
                 if (cudaLaunchHostFunc(srv->slots[slot], on_complete, c) != cudaSuccess) {
-                    // the request's arena block stays reserved until the server is destroyed
                     delete c;
                     cudaGetLastError();
+                    rc2 = EXSUM_ECUDA;
+                }
+            }
+            lock.lock();
+            if (rc) {
+                Request &q = srv->reqs[r.ticket];
+                q.status = rc;
+                if (rc2) {
+                    // the request's arena block stays reserved until the server is destroyed
                     srv->slot_busy[slot] = 0;
-                    r.done = true;
-                    r.t_done = now_ns();
+                    q.done = true;
+                    q.t_done = now_ns();
                     srv->cv_done.notify_all();
                 }
             }
         }
         if (srv->stop && srv->pending.empty()) break;
-        srv->cv_work.wait_for(lock, std::chrono::milliseconds(5));
+        if (wake_at) {
+            const int64_t dt = wake_at - now_ns();
+            if (dt > 0) srv->cv_work.wait_for(lock, std::chrono::nanoseconds(dt));
+        } else {
+            srv->cv_work.wait_for(lock, std::chrono::milliseconds(5));
+        }
     }
 }
 
@@ -260,7 +283,16 @@ exsum_server *exsum_server_create(size_t mem_budget_bytes, int max_slots)
     return srv;
 }
 
+int exsum_server_submit_at(exsum_server *srv, const exsum_desc *desc, int flags,
+                           int64_t arrival_ns, uint64_t *ticket);
+
 int exsum_server_submit(exsum_server *srv, const exsum_desc *desc, int flags, uint64_t *ticket)
+{
+    return exsum_server_submit_at(srv, desc, flags, 0, ticket);
+}
+
+int exsum_server_submit_at(exsum_server *srv, const exsum_desc *desc, int flags,
+                           int64_t arrival_ns, uint64_t *ticket)
 {
     if (!srv || !desc || !ticket) return EXSUM_EINVAL;
     if (flags & ~EXSUM_SERVE_HOST) return EXSUM_EINVAL;
@@ -283,7 +315,8 @@ int exsum_server_submit(exsum_server *srv, const exsum_desc *desc, int flags, ui
              ((r.out_bytes + 255) & ~(size_t)255);
     if (r.need == 0) r.need = 256;
     if (r.need > srv->budget) return EXSUM_ENOMEM;   // could never be admitted
-    r.t_submit = now_ns();
+    r.t_submit = arrival_ns > 0 ? arrival_ns : now_ns();
+    r.not_before = arrival_ns;
     {
         std::lock_guard<std::mutex> lock(srv->mu);
         if (srv->stop) return EXSUM_EBUSY;
@@ -336,6 +369,8 @@ int exsum_server_release(exsum_server *srv, uint64_t ticket)
     srv->reqs.erase(it);
     return EXSUM_OK;
 }
+
+int64_t exsum_server_now_ns(void) { return now_ns(); }
 
 int64_t exsum_server_completed(exsum_server *srv)
 {
