@@ -92,7 +92,9 @@ size_t exsum_workspace_bytes(int d, const int64_t *shape, const int64_t *k, int 
  * Arbitrary Dimensions"): the k-blocked Range-Prefix-Row / Range-Suffix-Row
  * scans and Combine-Along-Row of BDBS-1D applied along dimensions d, ..., 1
  * in turn (BDBS-Along-Dim, Sec. 5).  out[x] = (+) over the clipped box at x.
- * `out` has the output dtype and the same shape.  Uses a workspace that the
+ * `out` has the output dtype and the same shape; with two or more
+ * dimensions whose box side exceeds 1, `out` also holds intermediates during
+ * the call.  Uses a workspace that the
  * library allocates and caches per device (cudaMalloc on first use or
  * growth, outside any stream capture; a call made while `stream` is being
  * captured that would need to grow the cache returns EXSUM_EBUSY).
@@ -118,7 +120,9 @@ int exsum_included_ws(const void *in, void *out, int d, const int64_t *shape, co
  * prefix/suffix along dimension i (both reduce over product sets, so the
  * order is immaterial for a commutative operator), which needs one BDBS per
  * step instead of two; see the library's design notes.
- * Same arguments, ownership and workspace policy as exsum_included.
+ * Same arguments, ownership and workspace policy as exsum_included.  `out`
+ * is written exactly once, by the last kernel of the call, and is not used
+ * as scratch.
  */
 int exsum_excluded(const void *in, void *out, int d, const int64_t *shape, const int64_t *k,
                    int op, int dtype, void *stream);

@@ -189,6 +189,34 @@ using M_F32_MAX = MonFloatMax<float>;
 using M_BF16_ADD = MonFloatAdd<uint16_t>;
 using M_BF16_MAX = MonFloatMax<uint16_t>;
 
+// --- compensated local arithmetic ------------------------------------------------------
+// The same monoid with the long (compensated) accumulator used for the short
+// scans too.  Box-complement uses it for everything computed on carries: the
+// carries' included sums and the lower-dimensional recursion, whose values
+// are as large as the final sums.
+template <class M>
+struct MonComp {
+    using in_t = typename M::in_t;
+    using out_t = typename M::out_t;
+    using acc_t = typename M::acc_t;
+    using car_t = typename M::car_t;
+    using loc_t = acc_t;
+    static constexpr bool compensated = false;   // already the compensated form
+    __device__ __forceinline__ static acc_t id() { return M::id(); }
+    __device__ __forceinline__ static acc_t op(acc_t a, acc_t b) { return M::op(a, b); }
+    template <class V>
+    __device__ __forceinline__ static acc_t get(V v) { return M::get(v); }
+    template <class S>
+    __device__ __forceinline__ static S put(acc_t a) { return M::template put<S>(a); }
+    __device__ __forceinline__ static loc_t lid() { return M::id(); }
+    __device__ __forceinline__ static loc_t lop(loc_t a, loc_t b) { return M::op(a, b); }
+    template <class V>
+    __device__ __forceinline__ static loc_t lget(V v) { return M::get(v); }
+    __device__ __forceinline__ static acc_t widen(loc_t v) { return v; }
+    template <class S>
+    __device__ __forceinline__ static S lput(loc_t a) { return M::template put<S>(a); }
+};
+
 // --- warp shuffles of accumulator values ---------------------------------------------
 __device__ __forceinline__ int32_t shfl_up(int32_t v, int dl) { return __shfl_up_sync(0xffffffffu, v, dl); }
 __device__ __forceinline__ int64_t shfl_up(int64_t v, int dl)

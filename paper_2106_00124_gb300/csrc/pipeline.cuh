@@ -11,6 +11,8 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <type_traits>
+
 #include "kernels_flat.cuh"
 
 namespace exsum {
@@ -77,6 +79,8 @@ static inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 template <class M>
 struct Pipe {
+    // Monoid for work on carries (compensated local arithmetic for fp +).
+    using MC = typename std::conditional<M::compensated, MonComp<M>, M>::type;
     using A = typename M::acc_t;
     using IN = typename M::in_t;
     using OUT = typename M::out_t;
@@ -317,7 +321,10 @@ struct Pipe {
         int P = 0;
         for (int j = d - 1; j >= 1; --j)
             if (k[j] > 1) dims[P++] = j;
+        // H ping-pongs between two workspace buffers and ends in B; `out` is
+        // written once, by the last kernel, and never used as scratch.
         SOut *B = P > 0 ? cx.take<SOut>(N) : nullptr;
+        SOut *B2 = P > 1 ? cx.take<SOut>(N) : nullptr;
         CAR *R = cx.take<CAR>(S * M1);
         CAR *Rt = cx.take<CAR>(S * M1);
         CAR *G = cx.take<CAR>(M1);
@@ -329,8 +336,7 @@ struct Pipe {
         // The first pass fuses the segment totals of X when it is the
         // contiguous register pass over whole 32-row segments.
         const bool fused = P > 0 && dims[0] == d - 1 && k[d - 1] <= 32 && n[0] >= 32;
-        // H: BDBS along dims d..2, ping-ponging between out and B and ending in B.
-        // Pass 0 runs first; when it carries the segment totals, the carries,
+        // H: BDBS along dims d..2, ending in B.  Pass 0 runs first; when it carries the segment totals, the carries,
         // their included sums and the lower-dimensional recursion only depend
         // on it and run on the side stream while the other passes proceed.
         auto run_pass = [&](int p, const void *src) -> SOut * {
@@ -338,7 +344,7 @@ struct Pipe {
             int64_t O = 1, I = 1;
             for (int m = 0; m < j; ++m) O *= n[m];
             for (int m = j + 1; m < d; ++m) I *= n[m];
-            SOut *dst = ((P - 1 - p) % 2 == 0) ? B : out;
+            SOut *dst = ((P - 1 - p) % 2 == 0) ? B : B2;
             if (p == 0 && fused) {
                 if (!cx.dry && cx.ok()) {
                     const int64_t kk = k[j];
@@ -407,12 +413,12 @@ struct Pipe {
                 ks[m] = k[m];
             }
             CAR *Qo = cx.take<CAR>(S * M1);
-            included<CAR, CAR>(cx, Qa, Qo, d, ns, ks);
+            Pipe<MC>::template included<CAR, CAR>(cx, Qa, Qo, d, ns, ks);
             Qh = Qo;
         }
         if (fork2) cx.stream = aux->side2;
         cx.level++;
-        excluded<CAR, CAR>(cx, G, T, d - 1, n + 1, k + 1);
+        Pipe<MC>::template excluded<CAR, CAR>(cx, G, T, d - 1, n + 1, k + 1);
         cx.level--;
         // Join: the remaining passes on the caller's stream, then wait.
         cx.aux = aux;
