@@ -178,12 +178,12 @@ def pass_bytes(kernel, level, elems, dtype):
     """Algorithmic (compulsory) bytes of one launch: every element the pass
     must read once plus every element it must write once."""
     if level == 0:
-        rd = BYTES[dtype] if kernel in ("segment_reduce",) else OUT_BYTES[dtype]
+        rd = OUT_BYTES[dtype]
         wr = OUT_BYTES[dtype]
     else:
         car = 8 if dtype in ("f32", "bf16") else BYTES[dtype]
         rd = wr = car
-    if kernel == "bdbs_along_dim":
+    if kernel.startswith("bdbs_along_dim"):
         return elems * (rd + wr)
     if kernel == "dim1_prefix_suffix_contrib":
         return elems * (rd + wr)
@@ -364,8 +364,11 @@ def run_ours(args):
 
     # ---- CPU oracle baseline (rank 0, N = 1 only) ------------------------------------------------
     cpu = None
+    accuracy = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(vals, spec, budget_s=12.0)
+        cpu, ref = cpu_baseline(vals, spec, budget_s=12.0)
+        if ref is not None:
+            accuracy = accuracy_vs_oracle(out.cpu().numpy(), ref, dtype, op)
 
     if rank == 0:
         line = {
@@ -382,15 +385,43 @@ def run_ours(args):
                                    "frac": round(one_rw / (ms_per_step * 1e-3) / 1e9 / peak, 4)},
             "passes": passes,
             "e2e": e2e, "gpu_launches": launches, "clocks": clk, "cpu_baseline": cpu,
+            "accuracy": accuracy,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
 
 
+def accuracy_vs_oracle(got, ref, dtype, op):
+    """Error of the GPU result against the oracle's (fp64 / int64) result."""
+    import numpy as np
+    if dtype in ("i32", "i64") or op == "max":
+        want = ref
+        if dtype == "i32":
+            want = np.where(ref == np.iinfo(np.int64).min, np.iinfo(np.int32).min,
+                            ref).astype(np.int32) if op == "max" else ref.astype(np.int32)
+        elif dtype == "i64":
+            want = ref.astype(np.int64)
+        else:
+            want = ref.astype(np.float32)
+        return {"exact": bool(np.array_equal(got, want)),
+                "mismatches": int(np.count_nonzero(got != want))}
+    g = got.astype(np.float64).ravel()
+    r = ref.astype(np.float64).ravel()
+    rms = float(np.sqrt(np.mean(r * r)))
+    diff = np.abs(g - r)
+    floored = float(np.max(diff / np.maximum(np.abs(r), rms)))
+    nz = np.abs(r) > 0
+    return {"vs": "fp64 oracle", "max_rel_floored": floored,
+            "max_rel_unfloored": float(np.max(diff[nz] / np.abs(r[nz]))) if nz.any() else 0.0,
+            "normwise": float(np.linalg.norm(g - r) / max(np.linalg.norm(r), 1e-300)),
+            "tolerance": 1e-5, "within": floored <= 1e-5}
+
+
 def cpu_baseline(vals, spec, budget_s):
     """The CPU oracle's box-complement timed on this host, on whole tensors
-    of the workload when one run fits the budget, else on leading slabs."""
+    of the workload when one run fits the budget, else on leading slabs.
+    Returns (record, oracle result of the whole tensor or None)."""
     import numpy as np
     from oracle import oracle
     shape, k, op = spec["shape"], spec["k"], spec["op"]
@@ -404,11 +435,11 @@ def cpu_baseline(vals, spec, budget_s):
         runs = max(1, int(budget_s // (per_elem * N)))
         t0 = time.perf_counter()
         for _ in range(runs):
-            oracle.box_complement(vals, k, op)
+            ref = oracle.box_complement(vals, k, op)
         dt = time.perf_counter() - t0
-        return {"value": round(runs * N / dt / 1e9, 5), "unit": UNIT, "cores": 1, "kind": "oracle",
-                "sample": "%d run(s) of the whole %s tensor, single-threaded C oracle "
-                          "(box-complement)" % (runs, "x".join(map(str, shape)))}
+        return ({"value": round(runs * N / dt / 1e9, 5), "unit": UNIT, "cores": 1, "kind": "oracle",
+                 "sample": "%d run(s) of the whole %s tensor, single-threaded C oracle "
+                           "(box-complement)" % (runs, "x".join(map(str, shape)))}, ref)
     rows = max(1, int(budget_s / (per_elem * (N // shape[0]))))
     rows = min(rows, shape[0])
     slab = np.ascontiguousarray(vals[:rows])
@@ -416,9 +447,9 @@ def cpu_baseline(vals, spec, budget_s):
     t0 = time.perf_counter()
     oracle.box_complement(slab, kk, op)
     dt = time.perf_counter() - t0
-    return {"value": round(slab.size / dt / 1e9, 5), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "leading %d of %d slabs along dim 1, single-threaded C oracle" % (
-                rows, shape[0])}
+    return ({"value": round(slab.size / dt / 1e9, 5), "unit": UNIT, "cores": 1, "kind": "oracle",
+             "sample": "leading %d of %d slabs along dim 1, single-threaded C oracle" % (
+                 rows, shape[0])}, None)
 
 
 # ---- reference arm: the CPU oracle -------------------------------------------------------------

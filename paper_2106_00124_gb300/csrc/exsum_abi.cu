@@ -350,7 +350,9 @@ int exsum_trace_collect(int *tags, int *levels, int64_t *elems, float *ms, int c
 const char *exsum_kernel_name(int tag)
 {
     switch (tag) {
-    case exsum::TAG_INC: return "bdbs_along_dim";
+    case exsum::TAG_INC: return "bdbs_along_dim_lines";
+    case exsum::TAG_INC_CONTIG: return "bdbs_along_dim_contiguous";
+    case exsum::TAG_INC_STRIDED: return "bdbs_along_dim_strided";
     case exsum::TAG_REDUCE: return "segment_reduce";
     case exsum::TAG_SUMSEG: return "segment_totals";
     case exsum::TAG_CARRY: return "dim1_carries";

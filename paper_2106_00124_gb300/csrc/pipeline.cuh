@@ -22,12 +22,14 @@ enum { ST_OK = 0, ST_EINVAL = -1, ST_ENOMEM = -2, ST_EUNSUP = -3, ST_ECUDA = -4 
 
 // Kernel tags reported by the launch trace (exsum_trace_*).
 enum KernelTag {
-    TAG_INC = 0,       // BDBS-Along-Dim line pass
-    TAG_REDUCE = 1,    // segment / column reductions
-    TAG_SUMSEG = 2,    // segment totals -> column totals
-    TAG_CARRY = 3,     // dimension-1 carries
-    TAG_EXLINE = 4,    // dimension-1 prefix/suffix + contributions
-    TAG_COUNT = 5
+    TAG_INC = 0,          // BDBS-Along-Dim, generic line pass (k > 32)
+    TAG_REDUCE = 1,       // segment / column reductions
+    TAG_SUMSEG = 2,       // segment totals -> column totals
+    TAG_CARRY = 3,        // dimension-1 carries
+    TAG_EXLINE = 4,       // dimension-1 prefix/suffix + contributions
+    TAG_INC_CONTIG = 5,   // BDBS-Along-Dim, contiguous dimension (k_inc_flat)
+    TAG_INC_STRIDED = 6,  // BDBS-Along-Dim, strided dimension (k_inc_strided)
+    TAG_COUNT = 7
 };
 
 // Launch bracketing for the trace and the launch counter (exsum_abi.cu).
@@ -117,7 +119,7 @@ struct Pipe {
             }
             const int64_t nq = cdiv(M1, 128);
             const int64_t blocks = cdiv(pn1, 32) * nq;
-            cx.before(TAG_INC, N);
+            cx.before(TAG_INC_CONTIG, N);
             k_inc_flat<M, SIn, SOut, KMAX><<<(unsigned)blocks, 256, 0, cx.stream>>>(
                 src, dst, N, pn1, M1, n, (int)k, nq, Rsum, Rtail, r_tail);
             cx.check_launch();
@@ -128,7 +130,7 @@ struct Pipe {
             if (Lc > n) Lc = (int)n;
             const int nchunks = (int)cdiv(n, Lc);
             const int64_t total = O * nchunks * I;
-            cx.before(TAG_INC, O * n * I);
+            cx.before(TAG_INC_STRIDED, O * n * I);
             k_inc_strided<M, SIn, SOut, KMAX><<<(unsigned)cdiv(total, 128), 128, 0, cx.stream>>>(
                 src, dst, O, (int)n, I, (int)k, Lc, nchunks);
             cx.check_launch();
