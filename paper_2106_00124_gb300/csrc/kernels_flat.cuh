@@ -176,16 +176,33 @@ k_inc_flat(const SIn *__restrict__ in, SOut *__restrict__ out, int64_t N, int64_
         }
         __syncwarp();
         Lt o[4];
+        if (k == KMAX && pos0 + 3 + KMAX <= n) {
+            // All four windows are whole (no row end inside them): they share
+            // st[3 .. KMAX-1]; windows i and i+1 differ by one element at each
+            // end, so the four sums take about KMAX + 7 operations.
+            Lt m = st[3];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            int p = pos0 + i;
-            while (p >= n) p -= (int)n;
-            const int lim = min(k, (int)n - p);
-            Lt acc = st[i];
+            for (int j = 4; j < KMAX; ++j) m = M::lop(m, st[j]);
+            if constexpr (KMAX >= 4) {
+                const Lt a = M::lop(st[1], st[2]);
+                const Lt b = M::lop(st[KMAX], st[KMAX + 1]);
+                o[0] = M::lop(M::lop(st[0], a), m);
+                o[1] = M::lop(M::lop(a, m), st[KMAX]);
+                o[2] = M::lop(M::lop(st[2], m), b);
+                o[3] = M::lop(M::lop(m, b), st[KMAX + 2]);
+            }
+        } else {
 #pragma unroll
-            for (int j = 1; j < KMAX; ++j)
-                if (j < lim) acc = M::lop(acc, st[i + j]);
-            o[i] = acc;
+            for (int i = 0; i < 4; ++i) {
+                int p = pos0 + i;
+                while (p >= n) p -= (int)n;
+                const int lim = min(k, (int)n - p);
+                Lt acc = st[i];
+#pragma unroll
+                for (int j = 1; j < KMAX; ++j)
+                    if (j < lim) acc = M::lop(acc, st[i + j]);
+                o[i] = acc;
+            }
         }
         SOut *dst = out + base + 4 * lane;
         const bool vout = valid == 4 && (((uintptr_t)dst) & (4 * sizeof(SOut) - 1)) == 0;
