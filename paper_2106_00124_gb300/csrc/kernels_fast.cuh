@@ -66,10 +66,14 @@ k_inc_strided(const SIn *__restrict__ in, SOut *__restrict__ out, int64_t O, int
     SOut *dst = out + o * n * I + i;
     const int r0 = ch * Lc;
     const int rend = min(r0 + Lc, n);
+    const uint64_t pol_in = l2_policy_evict_first();
+    const uint64_t pol_out = l2_policy_evict_last();
     bdbs_walk<M, KMAX>(
         k, r0, rend,
-        [&](int x) { return x < n ? M::lget(src[(int64_t)x * I]) : M::lid(); },
-        [&](int x, typename M::loc_t v) { dst[(int64_t)x * I] = M::template lput<SOut>(v); });
+        [&](int x) { return x < n ? M::lget(ld_hint(src + (int64_t)x * I, pol_in)) : M::lid(); },
+        [&](int x, typename M::loc_t v) {
+            st_hint(dst + (int64_t)x * I, M::template lput<SOut>(v), pol_out);
+        });
 }
 
 // ---------------------------------------------------------------------------
@@ -289,6 +293,7 @@ k_exline2(const SIn *__restrict__ H, const typename M::car_t *__restrict__ Q, in
     const SIn *hp = H + s0 * Mc + c;
     const SIn *tp = hp + k1 * Mc;
     SOut *op_ = out + s0 * Mc + c;
+    const uint64_t pol_out = l2_policy_evict_first();   // final output: streamed out
     Lt P[L];
     Lt acc = M::lid();
     typename M::acc_t q = Q ? M::get(Q[s * qs + c]) : M::id();
@@ -311,7 +316,7 @@ k_exline2(const SIn *__restrict__ H, const typename M::car_t *__restrict__ Q, in
 #pragma unroll
         for (int t = L - 1; t >= 0; --t) {
             sacc = M::lop(tv[t], sacc);
-            op_[t * Mc] = M::template put<SOut>(M::op(q, M::widen(M::lop(P[t], sacc))));
+            st_hint(op_ + t * Mc, M::template put<SOut>(M::op(q, M::widen(M::lop(P[t], sacc)))), pol_out);
         }
     } else {
 #pragma unroll
@@ -390,6 +395,37 @@ k_carry_qa(const typename M::car_t *__restrict__ R, const typename M::car_t *__r
     using C = typename M::car_t;
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= Mc) return;
+    if (S <= 16) {
+        // Few segments: every load issued up front, all arithmetic in registers.
+        A r[16], rt[16];
+#pragma unroll
+        for (int s = 0; s < 16; ++s) {
+            r[s] = s < S ? M::get(R[s * Mc + c]) : M::id();
+            rt[s] = s < S ? M::get(Rt[s * Mc + c]) : M::id();
+        }
+        A sr[17];
+        sr[16] = M::id();
+#pragma unroll
+        for (int s = 15; s >= 0; --s) sr[s] = M::op(r[s], sr[s + 1]);
+        G[c] = M::template put<C>(sr[0]);
+        if (!Qa) return;
+        A pc = M::id();
+#pragma unroll
+        for (int s = 0; s < 16; ++s) {
+            if (s < S) {
+                const int64_t q = s + qoff;
+                A w = M::id();
+                if (q < S) {
+#pragma unroll
+                    for (int qq = 0; qq < 16; ++qq)
+                        if (qq == q) w = M::op(rt[qq], sr[qq + 1]);
+                }
+                Qa[s * Mc + c] = M::template put<C>(M::op(pc, w));
+                pc = M::op(pc, r[s]);
+            }
+        }
+        return;
+    }
     // Backward: suffix totals SR[s] parked in Qa.
     A acc = M::id();
     for (int64_t s = S - 1; s >= 0; --s) {

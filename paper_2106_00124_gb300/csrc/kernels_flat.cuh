@@ -25,19 +25,20 @@ __device__ __forceinline__ void cp_async_elem(T *sdst, const T *gsrc)
 // Four consecutive elements starting at p (16-byte-aligned vector access when
 // `vec`, else scalar), converted to the local accumulator type.
 template <class M, class SIn>
-__device__ __forceinline__ void load4(const SIn *p, bool vec, int valid, typename M::loc_t v[4])
+__device__ __forceinline__ void load4(const SIn *p, bool vec, int valid, typename M::loc_t v[4],
+                                      uint64_t pol)
 {
     if (vec) {
         SIn t[4];
         if constexpr (sizeof(SIn) * 4 == 16) {
-            const uint4 r = *reinterpret_cast<const uint4 *>(p);
+            const uint4 r = ld_hint_v4(p, pol);
             memcpy(t, &r, 16);
         } else if constexpr (sizeof(SIn) * 4 == 8) {
-            const uint2 r = *reinterpret_cast<const uint2 *>(p);
+            const uint2 r = ld_hint_v2(p, pol);
             memcpy(t, &r, 8);
         } else {
-            const uint4 r0 = reinterpret_cast<const uint4 *>(p)[0];
-            const uint4 r1 = reinterpret_cast<const uint4 *>(p)[1];
+            const uint4 r0 = ld_hint_v4(p, pol);
+            const uint4 r1 = ld_hint_v4(reinterpret_cast<const uint4 *>(p) + 1, pol);
             memcpy(t, &r0, 16);
             memcpy(t + 2, &r1, 16);
         }
@@ -45,12 +46,13 @@ __device__ __forceinline__ void load4(const SIn *p, bool vec, int valid, typenam
         for (int i = 0; i < 4; ++i) v[i] = M::lget(t[i]);
     } else {
 #pragma unroll
-        for (int i = 0; i < 4; ++i) v[i] = i < valid ? M::lget(p[i]) : M::lid();
+        for (int i = 0; i < 4; ++i) v[i] = i < valid ? M::lget(ld_hint(p + i, pol)) : M::lid();
     }
 }
 
 template <class M, class SOut>
-__device__ __forceinline__ void store4(SOut *p, bool vec, int valid, const typename M::loc_t v[4])
+__device__ __forceinline__ void store4(SOut *p, bool vec, int valid, const typename M::loc_t v[4],
+                                       uint64_t pol)
 {
     SOut t[4];
 #pragma unroll
@@ -59,18 +61,18 @@ __device__ __forceinline__ void store4(SOut *p, bool vec, int valid, const typen
         if constexpr (sizeof(SOut) * 4 == 16) {
             uint4 r;
             memcpy(&r, t, 16);
-            *reinterpret_cast<uint4 *>(p) = r;
+            st_hint_v4(p, r, pol);
         } else {
             uint4 r0, r1;
             memcpy(&r0, t, 16);
             memcpy(&r1, t + 2, 16);
-            reinterpret_cast<uint4 *>(p)[0] = r0;
-            reinterpret_cast<uint4 *>(p)[1] = r1;
+            st_hint_v4(p, r0, pol);
+            st_hint_v4(reinterpret_cast<uint4 *>(p) + 1, r1, pol);
         }
     } else {
 #pragma unroll
         for (int i = 0; i < 4; ++i)
-            if (i < valid) p[i] = t[i];
+            if (i < valid) st_hint(p + i, t[i], pol);
     }
 }
 
@@ -123,6 +125,8 @@ k_inc_flat(const SIn *__restrict__ in, SOut *__restrict__ out, int64_t N, int64_
     const int64_t col = c0 + 4 * lane;
     const int pos0 = (int)(col % n);
     Lt *sb = buf[warp];
+    const uint64_t pol_in = l2_policy_evict_first();   // the input is read once
+    const uint64_t pol_out = l2_policy_evict_last();   // the next pass reads the output
     for (int u = warp; u < SEG; u += WARPS) {
         const int64_t x1 = s * SEG + u;
         if (x1 >= n1) break;
@@ -133,7 +137,7 @@ k_inc_flat(const SIn *__restrict__ in, SOut *__restrict__ out, int64_t N, int64_
         const int valid = (int)max((int64_t)0, min((int64_t)4, lim_c - 4 * lane));
         const SIn *src = in + base + 4 * lane;
         const bool vin = valid == 4 && (((uintptr_t)src) & (4 * sizeof(SIn) - 1)) == 0;
-        load4<M>(src, vin, valid, v);
+        load4<M>(src, vin, valid, v, pol_in);
         // 16-byte (or 2 x 16-byte) shared stores: no bank conflicts
         if constexpr (sizeof(Lt) == 4) {
             float4 w;
@@ -206,7 +210,7 @@ k_inc_flat(const SIn *__restrict__ in, SOut *__restrict__ out, int64_t N, int64_
         }
         SOut *dst = out + base + 4 * lane;
         const bool vout = valid == 4 && (((uintptr_t)dst) & (4 * sizeof(SOut) - 1)) == 0;
-        if (valid > 0) store4<M>(dst, vout, valid, o);
+        if (valid > 0) store4<M>(dst, vout, valid, o, pol_out);
     }
     if (sums) {
 #pragma unroll

@@ -28,6 +28,7 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 namespace exsum {
 
@@ -216,6 +217,84 @@ struct MonComp {
     template <class S>
     __device__ __forceinline__ static S lput(loc_t a) { return M::template put<S>(a); }
 };
+
+// --- L2 eviction-priority hints ---------------------------------------------------------
+// Passes hand their output to the next pass through global memory.  When the
+// tensor fits in L2 (129 MB on GB300), writing such intermediates with the
+// evict_last priority and reading inputs used once with evict_first lets the
+// next pass find them in L2 instead of HBM.  Hints only: results do not
+// depend on them.
+__device__ __forceinline__ uint64_t l2_policy_evict_last()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;\n" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t l2_policy_evict_first()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;\n" : "=l"(p));
+    return p;
+}
+
+template <class T>
+__device__ __forceinline__ T ld_hint(const T *p, uint64_t pol)
+{
+    static_assert(sizeof(T) == 2 || sizeof(T) == 4 || sizeof(T) == 8, "element size");
+    T v;
+    if constexpr (sizeof(T) == 4) {
+        uint32_t r;
+        asm volatile("ld.global.L2::cache_hint.b32 %0, [%1], %2;\n" : "=r"(r) : "l"(p), "l"(pol));
+        memcpy(&v, &r, 4);
+    } else if constexpr (sizeof(T) == 8) {
+        uint64_t r;
+        asm volatile("ld.global.L2::cache_hint.b64 %0, [%1], %2;\n" : "=l"(r) : "l"(p), "l"(pol));
+        memcpy(&v, &r, 8);
+    } else {
+        uint16_t r;
+        asm volatile("ld.global.L2::cache_hint.b16 %0, [%1], %2;\n" : "=h"(r) : "l"(p), "l"(pol));
+        memcpy(&v, &r, 2);
+    }
+    return v;
+}
+
+template <class T>
+__device__ __forceinline__ void st_hint(T *p, T v, uint64_t pol)
+{
+    static_assert(sizeof(T) == 4 || sizeof(T) == 8, "element size");
+    if constexpr (sizeof(T) == 4) {
+        uint32_t r;
+        memcpy(&r, &v, 4);
+        asm volatile("st.global.L2::cache_hint.b32 [%0], %1, %2;\n" ::"l"(p), "r"(r), "l"(pol) : "memory");
+    } else {
+        uint64_t r;
+        memcpy(&r, &v, 8);
+        asm volatile("st.global.L2::cache_hint.b64 [%0], %1, %2;\n" ::"l"(p), "l"(r), "l"(pol) : "memory");
+    }
+}
+
+__device__ __forceinline__ uint4 ld_hint_v4(const void *p, uint64_t pol)
+{
+    uint4 r;
+    asm volatile("ld.global.L2::cache_hint.v4.b32 {%0, %1, %2, %3}, [%4], %5;\n"
+                 : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+                 : "l"(p), "l"(pol));
+    return r;
+}
+__device__ __forceinline__ uint2 ld_hint_v2(const void *p, uint64_t pol)
+{
+    uint2 r;
+    asm volatile("ld.global.L2::cache_hint.v2.b32 {%0, %1}, [%2], %3;\n"
+                 : "=r"(r.x), "=r"(r.y)
+                 : "l"(p), "l"(pol));
+    return r;
+}
+__device__ __forceinline__ void st_hint_v4(void *p, uint4 r, uint64_t pol)
+{
+    asm volatile("st.global.L2::cache_hint.v4.b32 [%0], {%1, %2, %3, %4}, %5;\n" ::"l"(p), "r"(r.x),
+                 "r"(r.y), "r"(r.z), "r"(r.w), "l"(pol)
+                 : "memory");
+}
 
 // --- warp shuffles of accumulator values ---------------------------------------------
 __device__ __forceinline__ int32_t shfl_up(int32_t v, int dl) { return __shfl_up_sync(0xffffffffu, v, dl); }
