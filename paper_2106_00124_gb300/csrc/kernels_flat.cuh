@@ -127,17 +127,33 @@ k_inc_flat(const SIn *__restrict__ in, SOut *__restrict__ out, int64_t N, int64_
     Lt *sb = buf[warp];
     const uint64_t pol_in = l2_policy_evict_first();   // the input is read once
     const uint64_t pol_out = l2_policy_evict_last();   // the next pass reads the output
-    for (int u = warp; u < SEG; u += WARPS) {
+    // Plane-invariant lane geometry: every plane but a partial last one (only
+    // without segment totals, when planes pack whole rows) has the same extent.
+    const int64_t full_c = M1 - c0;                      // chunk elements that exist
+    const int valid_full = (int)max((int64_t)0, min((int64_t)4, full_c - 4 * lane));
+    const bool halo_full = CH + lane < full_c;
+    const bool aligned_stride = ((M1 * (int64_t)sizeof(SIn)) & 15) == 0 &&
+                                ((M1 * (int64_t)sizeof(SOut)) & 15) == 0;
+    const bool fast = (k == KMAX) && (pos0 + 3 + KMAX <= n);
+    const SIn *src = in + (s * SEG + warp) * M1 + c0 + 4 * lane;
+    SOut *dst = out + (s * SEG + warp) * M1 + c0 + 4 * lane;
+    const int64_t step = (int64_t)WARPS * M1;
+    const bool vin0 = aligned_stride && ((((uintptr_t)src) & (4 * sizeof(SIn) - 1)) == 0);
+    const bool vout0 = aligned_stride && ((((uintptr_t)dst) & (4 * sizeof(SOut) - 1)) == 0);
+    for (int u = warp; u < SEG; u += WARPS, src += step, dst += step) {
         const int64_t x1 = s * SEG + u;
         if (x1 >= n1) break;
-        const int64_t base = x1 * M1 + c0;          // flat index of the chunk start
-        const int64_t lim_c = min(M1 - c0, N - base); // elements of the chunk that exist
+        int valid = valid_full;
+        bool halo = halo_full;
+        if (x1 == n1 - 1) {
+            // a partial last plane: clip the chunk at the end of the tensor
+            const int64_t lim_c = min(full_c, N - (x1 * M1 + c0));
+            valid = (int)max((int64_t)0, min((int64_t)4, lim_c - 4 * lane));
+            halo = CH + lane < lim_c;
+        }
         // stage the chunk and its halo (e past the plane or the tensor)
         Lt v[4];
-        const int valid = (int)max((int64_t)0, min((int64_t)4, lim_c - 4 * lane));
-        const SIn *src = in + base + 4 * lane;
-        const bool vin = valid == 4 && (((uintptr_t)src) & (4 * sizeof(SIn) - 1)) == 0;
-        load4<M>(src, vin, valid, v, pol_in);
+        load4<M>(src, vin0 && valid == 4, valid, v, pol_in);
         // 16-byte (or 2 x 16-byte) shared stores: no bank conflicts
         if constexpr (sizeof(Lt) == 4) {
             float4 w;
@@ -147,7 +163,8 @@ k_inc_flat(const SIn *__restrict__ in, SOut *__restrict__ out, int64_t N, int64_
 #pragma unroll
             for (int i = 0; i < 4; ++i) sb[4 * lane + i] = v[i];
         }
-        sb[CH + lane] = (CH + lane < lim_c) ? M::lget(in[base + CH + lane]) : M::lid();
+        // halo element CH + lane of the chunk (src points at element 4 * lane)
+        sb[CH + lane] = halo ? M::lget(ld_hint(src + (CH - 3 * lane), pol_in)) : M::lid();
         __syncwarp();
         if (sums) {
 #pragma unroll
@@ -180,21 +197,19 @@ k_inc_flat(const SIn *__restrict__ in, SOut *__restrict__ out, int64_t N, int64_
         }
         __syncwarp();
         Lt o[4];
-        if (k == KMAX && pos0 + 3 + KMAX <= n) {
+        if (fast) {
             // All four windows are whole (no row end inside them): they share
             // st[3 .. KMAX-1]; windows i and i+1 differ by one element at each
             // end, so the four sums take about KMAX + 7 operations.
             Lt m = st[3];
 #pragma unroll
             for (int j = 4; j < KMAX; ++j) m = M::lop(m, st[j]);
-            if constexpr (KMAX >= 4) {
-                const Lt a = M::lop(st[1], st[2]);
-                const Lt b = M::lop(st[KMAX], st[KMAX + 1]);
-                o[0] = M::lop(M::lop(st[0], a), m);
-                o[1] = M::lop(M::lop(a, m), st[KMAX]);
-                o[2] = M::lop(M::lop(st[2], m), b);
-                o[3] = M::lop(M::lop(m, b), st[KMAX + 2]);
-            }
+            const Lt a = M::lop(st[1], st[2]);
+            const Lt b = M::lop(st[KMAX], st[KMAX + 1]);
+            o[0] = M::lop(M::lop(st[0], a), m);
+            o[1] = M::lop(M::lop(a, m), st[KMAX]);
+            o[2] = M::lop(M::lop(st[2], m), b);
+            o[3] = M::lop(M::lop(m, b), st[KMAX + 2]);
         } else {
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
@@ -208,9 +223,7 @@ k_inc_flat(const SIn *__restrict__ in, SOut *__restrict__ out, int64_t N, int64_
                 o[i] = acc;
             }
         }
-        SOut *dst = out + base + 4 * lane;
-        const bool vout = valid == 4 && (((uintptr_t)dst) & (4 * sizeof(SOut) - 1)) == 0;
-        if (valid > 0) store4<M>(dst, vout, valid, o, pol_out);
+        if (valid > 0) store4<M>(dst, vout0 && valid == 4, valid, o, pol_out);
     }
     if (sums) {
 #pragma unroll
