@@ -185,7 +185,7 @@ def pass_bytes(kernel, level, elems, dtype):
         rd = wr = car
     if kernel.startswith("bdbs_along_dim"):
         return elems * (rd + wr)
-    if kernel == "dim1_prefix_suffix_contrib":
+    if kernel in ("dim1_prefix_suffix_contrib", "row_prefix_suffix_contrib"):
         return elems * (rd + wr)
     if kernel == "segment_reduce":
         return elems * rd

@@ -5,6 +5,7 @@
 #include <atomic>
 #include <map>
 #include <mutex>
+#include <cstdlib>
 #include <utility>
 #include <vector>
 
@@ -128,8 +129,11 @@ static const exsum::Aux *aux_for(void *stream)
         return nullptr;
     }
     exsum::Aux a;
-    if (cudaStreamCreateWithFlags(&a.side, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&a.side2, cudaStreamNonBlocking) != cudaSuccess ||
+    int lo = 0, hi = 0;
+    cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    int prio = getenv("EXSUM_EXP_PRIO") ? hi : 0;
+    if (cudaStreamCreateWithPriority(&a.side, cudaStreamNonBlocking, prio) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&a.side2, cudaStreamNonBlocking, prio) != cudaSuccess ||
         cudaEventCreateWithFlags(&a.fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&a.join, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&a.fork2, cudaEventDisableTiming) != cudaSuccess ||
@@ -357,6 +361,8 @@ const char *exsum_kernel_name(int tag)
     case exsum::TAG_SUMSEG: return "segment_totals";
     case exsum::TAG_CARRY: return "dim1_carries";
     case exsum::TAG_EXLINE: return "dim1_prefix_suffix_contrib";
+    case exsum::TAG_ROWSUM: return "row_totals";
+    case exsum::TAG_ROWX: return "row_prefix_suffix_contrib";
     default: return "unknown";
     }
 }

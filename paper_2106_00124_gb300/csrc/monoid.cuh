@@ -327,4 +327,45 @@ __device__ __forceinline__ f2 shfl_down(f2 v, int dl)
     return r;
 }
 
+// Segmented variants: lanes exchange only within aligned groups of `w` lanes.
+__device__ __forceinline__ int32_t shfl_up_w(int32_t v, int dl, int w) { return __shfl_up_sync(0xffffffffu, v, dl, w); }
+__device__ __forceinline__ int64_t shfl_up_w(int64_t v, int dl, int w)
+{
+    return (int64_t)__shfl_up_sync(0xffffffffu, (long long)v, dl, w);
+}
+__device__ __forceinline__ float shfl_up_w(float v, int dl, int w) { return __shfl_up_sync(0xffffffffu, v, dl, w); }
+__device__ __forceinline__ f2 shfl_up_w(f2 v, int dl, int w)
+{
+    f2 r;
+    r.hi = __shfl_up_sync(0xffffffffu, v.hi, dl, w);
+    r.lo = __shfl_up_sync(0xffffffffu, v.lo, dl, w);
+    return r;
+}
+__device__ __forceinline__ int32_t shfl_down_w(int32_t v, int dl, int w) { return __shfl_down_sync(0xffffffffu, v, dl, w); }
+__device__ __forceinline__ int64_t shfl_down_w(int64_t v, int dl, int w)
+{
+    return (int64_t)__shfl_down_sync(0xffffffffu, (long long)v, dl, w);
+}
+__device__ __forceinline__ float shfl_down_w(float v, int dl, int w) { return __shfl_down_sync(0xffffffffu, v, dl, w); }
+__device__ __forceinline__ f2 shfl_down_w(f2 v, int dl, int w)
+{
+    f2 r;
+    r.hi = __shfl_down_sync(0xffffffffu, v.hi, dl, w);
+    r.lo = __shfl_down_sync(0xffffffffu, v.lo, dl, w);
+    return r;
+}
+__device__ __forceinline__ int32_t shfl_xor(int32_t v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
+__device__ __forceinline__ int64_t shfl_xor(int64_t v, int m)
+{
+    return (int64_t)__shfl_xor_sync(0xffffffffu, (long long)v, m);
+}
+__device__ __forceinline__ float shfl_xor(float v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
+__device__ __forceinline__ f2 shfl_xor(f2 v, int m)
+{
+    f2 r;
+    r.hi = __shfl_xor_sync(0xffffffffu, v.hi, m);
+    r.lo = __shfl_xor_sync(0xffffffffu, v.lo, m);
+    return r;
+}
+
 }  // namespace exsum

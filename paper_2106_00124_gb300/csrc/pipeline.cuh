@@ -14,6 +14,7 @@
 #include <type_traits>
 
 #include "kernels_flat.cuh"
+#include "kernels_rows.cuh"
 
 namespace exsum {
 
@@ -29,7 +30,9 @@ enum KernelTag {
     TAG_EXLINE = 4,       // dimension-1 prefix/suffix + contributions
     TAG_INC_CONTIG = 5,   // BDBS-Along-Dim, contiguous dimension (k_inc_flat)
     TAG_INC_STRIDED = 6,  // BDBS-Along-Dim, strided dimension (k_inc_strided)
-    TAG_COUNT = 7
+    TAG_ROWSUM = 7,       // row totals over the last dimension (k_row_totals)
+    TAG_ROWX = 8,         // last-dimension prefix/suffix + contributions (k_rowx)
+    TAG_COUNT = 9
 };
 
 // Launch bracketing for the trace and the launch counter (exsum_abi.cu).
@@ -296,6 +299,216 @@ struct Pipe {
         }
     }
 
+    // ---- excluded sums with the last dimension peeled (kernels_rows.cuh) ---------------------
+    //
+    // Level with input X of shape n[0..d-1], L = n[d-1]:
+    //   R  = total of X over dimension d                          (dimension reduction)
+    //   T  = excluded sum of R with box k[0..d-2]                 (next level)
+    //   H  = included sum of X along dimensions 1..d-1            (BDBS-Along-Dim)
+    //   out[x] = T[x_1..x_{d-1}] (+) prefix of H's row before x_d (+) suffix of the row from x_d+k_d
+    // The rows are short enough for one warp to scan a row from shared memory,
+    // so this needs no carries; the window along dimension d-1 is fused into
+    // the final pass when its tile holds enough rows.
+    static constexpr int ROWX_THREADS = 256;
+
+    struct RowPlan {
+        bool ok = false, fuse = false;
+        int GO = 1, TR = 1, ntile = 1, RS = 1, RSA = 1, LS = 16, lpr = 32, epl = 4;
+        size_t smem = 0;
+    };
+
+    static int row_lanes(int64_t L)
+    {
+        const int64_t q4 = cdiv(L, 4);
+        int lpr = 1;
+        while (lpr < q4 && lpr < 32) lpr <<= 1;
+        return lpr;
+    }
+
+    // Tile geometry of the final pass: GO slices x TR rows per block.  The
+    // window along n_{d-1} is fused when the staged halo (k2 - 1 rows) is at
+    // most about half the tile, or the tile is the whole slice; small tensors
+    // get shorter tiles (more blocks) down to that limit.
+    static RowPlan row_plan(int d, const int64_t *n, const int64_t *k)
+    {
+        RowPlan rp;
+        if (d < 2) return rp;
+        const int64_t L = n[d - 1];
+        const int64_t s = (int64_t)sizeof(L_);
+        const int64_t lmax = s > 4 ? 512 : 1024;
+        if (L < 16 || L > lmax || n[d - 2] >= (1ll << 30)) return rp;
+        int64_t O2 = 1;
+        for (int m = 0; m < d - 2; ++m) O2 *= n[m];
+        const int64_t n2 = n[d - 2], k2 = k[d - 2];
+        const int64_t CE = 16 / s;
+        const int64_t LS = cdiv(L, 8 * CE) * 8 * CE;
+        const int64_t L32 = cdiv(L, 32) * 32;
+        const int64_t LPs = L32 + 4 * (L32 / 32) + 4;
+        const int64_t lpr = row_lanes(L);
+        int64_t epl = 4;   // 4, 8, 16 or 32 elements per lane
+        while (epl * lpr < L) epl <<= 1;
+        const int64_t rpw = 32 / lpr;
+        int64_t GO = ROWX_THREADS / L;
+        if (GO < 1) GO = 1;
+        if (GO > O2) GO = O2;
+        const int64_t groups = cdiv(O2, GO);
+        // rows per tile for at least two blocks per SM, when the tensor has them
+        const int64_t tr_par = groups >= 2 * 152 ? n2 : cdiv(n2, cdiv(2 * 152, groups));
+        auto fit = [&](int64_t budget, bool f, int64_t &TR, int64_t &ntile) -> bool {
+            // rows held: the tile, k2 - 1 halo rows and the identity rows the
+            // column walk may read past them (at most 2 k2 rows past the tile)
+            int64_t trmax = budget / (GO * LS * s) - (f ? 2 * k2 : 0);
+            int64_t cap = f ? (tr_par > 2 * k2 ? tr_par : 2 * k2) : tr_par;
+            if (cap > 64) cap = 64;
+            if (trmax > cap) trmax = cap;
+            if (trmax >= 16) trmax &= ~(int64_t)7;
+            if (trmax < 1) return false;
+            ntile = cdiv(n2, trmax);
+            TR = cdiv(n2, ntile);
+            return !f || ntile == 1 || TR >= 2 * k2;
+        };
+        int64_t TR = 1, ntile = 1;
+        bool fuse = false;
+        if (k2 > 1 && k2 <= 32)
+            fuse = fit(48 * 1024, true, TR, ntile) || fit(100 * 1024, true, TR, ntile);
+        if (!fuse && !fit(44 * 1024, false, TR, ntile)) return rp;
+        if (groups * ntile >= (1ll << 31)) return rp;
+        rp.ok = true;
+        rp.fuse = fuse;
+        rp.GO = (int)GO;
+        rp.TR = (int)TR;
+        rp.ntile = (int)ntile;
+        rp.RS = (int)(fuse ? TR + k2 - 1 : TR);
+        rp.RSA = (int)(fuse ? (TR - 1) / k2 * k2 + 2 * k2 : TR);
+        rp.LS = (int)LS;
+        rp.lpr = (int)lpr;
+        rp.epl = (int)epl;
+        rp.smem = (size_t)(GO * rp.RSA * LS + (ROWX_THREADS / 32) * rpw * LPs) * s;
+        return rp;
+    }
+
+    template <class SF, class SOut, int KM, int EPL>
+    static void rowx_epl(Ctx &cx, const RowPlan &rp, const SF *src, const CAR *T, SOut *out,
+                         int64_t O2, int64_t n2, int64_t L, int kk, int k3)
+    {
+        auto kern = k_rowx<M, SF, SOut, KM, EPL>;
+        if (rp.smem > 48 * 1024)
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rp.smem);
+        const unsigned blocks = (unsigned)(cdiv(O2, rp.GO) * rp.ntile);
+        kern<<<blocks, ROWX_THREADS, rp.smem, cx.stream>>>(src, T, out, O2, (int)n2, (int)L, kk, k3,
+                                                          rp.TR, rp.GO, rp.ntile, rp.RS, rp.RSA,
+                                                          rp.LS, rp.lpr);
+    }
+
+    template <class SF, class SOut, int KM>
+    static void rowx_go(Ctx &cx, const RowPlan &rp, const SF *src, const CAR *T, SOut *out,
+                        int64_t O2, int64_t n2, int64_t L, int kk, int k3)
+    {
+        if (rp.epl == 4)
+            rowx_epl<SF, SOut, KM, 4>(cx, rp, src, T, out, O2, n2, L, kk, k3);
+        else if (rp.epl == 8)
+            rowx_epl<SF, SOut, KM, 8>(cx, rp, src, T, out, O2, n2, L, kk, k3);
+        else if (rp.epl == 16)
+            rowx_epl<SF, SOut, KM, 16>(cx, rp, src, T, out, O2, n2, L, kk, k3);
+        else if (rp.epl == 32 && sizeof(L_) == 4)
+            rowx_epl<SF, SOut, KM, (sizeof(L_) == 4 ? 32 : 16)>(cx, rp, src, T, out, O2, n2, L, kk, k3);
+        else if (cx.status == ST_OK)
+            cx.status = ST_EUNSUP;  // not reachable: row_plan gives one of the widths above
+    }
+
+    template <class SF, class SOut>
+    static void rowx_launch(Ctx &cx, const RowPlan &rp, const SF *src, const CAR *T, SOut *out,
+                            int64_t O2, int64_t n2, int64_t L, int64_t k2, int64_t k3)
+    {
+        if (cx.dry || !cx.ok()) return;
+        cx.before(TAG_ROWX, O2 * n2 * L);
+        const int kk = rp.fuse ? (int)k2 : 1;
+        if (!rp.fuse)
+            rowx_go<SF, SOut, 1>(cx, rp, src, T, out, O2, n2, L, 1, (int)k3);
+        else if (kk <= 4)
+            rowx_go<SF, SOut, 4>(cx, rp, src, T, out, O2, n2, L, kk, (int)k3);
+        else if (kk <= 8)
+            rowx_go<SF, SOut, 8>(cx, rp, src, T, out, O2, n2, L, kk, (int)k3);
+        else if (kk <= 16)
+            rowx_go<SF, SOut, 16>(cx, rp, src, T, out, O2, n2, L, kk, (int)k3);
+        else
+            rowx_go<SF, SOut, 32>(cx, rp, src, T, out, O2, n2, L, kk, (int)k3);
+        cx.check_launch();
+    }
+
+
+    template <class SIn, class SOut>
+    static void excluded_rows(Ctx &cx, const RowPlan &rp, const SIn *X, SOut *out, int d,
+                              const int64_t *n, const int64_t *k)
+    {
+        int64_t N = 1;
+        for (int i = 0; i < d; ++i) N *= n[i];
+        const int64_t L = n[d - 1], rows = N / L, n2 = n[d - 2], O2 = rows / n2;
+        // BDBS passes before the final one: dimensions 1..d-2, and d-1 unless
+        // the final pass takes its window.
+        int dims[16];
+        int P = 0;
+        for (int j = 0; j < d - 2; ++j)
+            if (k[j] > 1) dims[P++] = j;
+        if (k[d - 2] > 1 && !rp.fuse) dims[P++] = d - 2;
+        SOut *B = P > 0 ? cx.take<SOut>(N) : nullptr;
+        SOut *B2 = P > 1 ? cx.take<SOut>(N) : nullptr;
+        CAR *R = cx.take<CAR>(rows);
+        CAR *T = cx.take<CAR>(rows);
+        // Row totals and the lower-dimensional recursion run on the side
+        // stream while the BDBS passes run on the caller's.
+        const Aux *aux = cx.aux;
+        const bool fork = P > 0 && aux && aux->side && !cx.dry && cx.ok();
+        cudaStream_t main_stream = cx.stream;
+        if (fork) {
+            cudaEventRecord(aux->fork, main_stream);
+            cudaStreamWaitEvent(aux->side, aux->fork, 0);
+            cx.stream = aux->side;
+        }
+        cx.aux = nullptr;
+        if (!cx.dry && cx.ok()) {
+            cx.before(TAG_ROWSUM, N);
+            const int lpr = row_lanes(L);
+            int64_t blocks = cdiv(rows, 8 * (32 / lpr));
+            if (blocks > 152 * 8) blocks = 152 * 8;
+            if (lpr <= 4)
+                k_row_totals<M, SIn, 4><<<(unsigned)blocks, 256, 0, cx.stream>>>(X, R, rows, (int)L);
+            else if (lpr == 8)
+                k_row_totals<M, SIn, 8><<<(unsigned)blocks, 256, 0, cx.stream>>>(X, R, rows, (int)L);
+            else if (lpr == 16)
+                k_row_totals<M, SIn, 16><<<(unsigned)blocks, 256, 0, cx.stream>>>(X, R, rows, (int)L);
+            else
+                k_row_totals<M, SIn, 32><<<(unsigned)blocks, 256, 0, cx.stream>>>(X, R, rows, (int)L);
+            cx.check_launch();
+        }
+        cx.level++;
+        Pipe<MC>::template excluded<CAR, CAR>(cx, R, T, d - 1, n, k);
+        cx.level--;
+        cx.aux = aux;
+        if (fork) {
+            cudaEventRecord(aux->join, aux->side);
+            cx.stream = main_stream;
+        }
+        const void *cur = X;
+        for (int p = 0; p < P; ++p) {
+            const int j = dims[p];
+            int64_t O = 1, I = 1;
+            for (int m = 0; m < j; ++m) O *= n[m];
+            for (int m = j + 1; m < d; ++m) I *= n[m];
+            SOut *dst = ((P - 1 - p) % 2 == 0) ? B : B2;
+            if (p == 0)
+                inc_pass<SIn, SOut>(cx, (const SIn *)cur, dst, O, n[j], I, k[j]);
+            else
+                inc_pass<SOut, SOut>(cx, (const SOut *)cur, dst, O, n[j], I, k[j]);
+            cur = dst;
+        }
+        if (fork) cudaStreamWaitEvent(main_stream, aux->join, 0);
+        if (P > 0)
+            rowx_launch<SOut, SOut>(cx, rp, (const SOut *)cur, T, out, O2, n2, L, k[d - 2], k[d - 1]);
+        else
+            rowx_launch<SIn, SOut>(cx, rp, (const SIn *)cur, T, out, O2, n2, L, k[d - 2], k[d - 1]);
+    }
+
     // ---- excluded sums: box-complement, one dimension-reduction step per level ---------------
     //
     // Level with input X of shape n[0..d-1]:
@@ -316,6 +529,11 @@ struct Pipe {
         const int64_t M1 = N / n[0];
         if (d == 1) {
             exline_stage<SIn, SOut>(cx, X, nullptr, out, n[0], 1, k[0]);
+            return;
+        }
+        const RowPlan rp = row_plan(d, n, k);
+        if (rp.ok) {
+            excluded_rows<SIn, SOut>(cx, rp, X, out, d, n, k);
             return;
         }
         const int64_t S = cdiv(n[0], EXL);

@@ -39,6 +39,23 @@ CASES = [
     ((3, 517), (2, 32)),
     ((70, 300), (33, 31)),
     ((7, 129, 131), (7, 17, 9)),
+    # last dimension peeled first (rows of 16 .. 1024): several slices per
+    # block with a ragged last group, several row tiles with the window along
+    # dimension d-1 fused (widths up to 32) or run as its own pass, k_d = 1,
+    # k_d = n_d, strips that do not fill 4-element vectors
+    ((33, 16), (7, 16)),
+    ((29, 3, 20), (3, 2, 5)),
+    ((3, 100, 256), (2, 9, 17)),
+    ((130, 64), (20, 5)),
+    ((12, 40), (9, 3)),
+    ((3, 1024), (2, 100)),
+    ((4, 257), (3, 256)),
+    ((20, 50), (4, 1)),
+    ((3, 4, 5, 40), (2, 3, 4, 7)),
+    ((4, 5, 64), (1, 1, 8)),
+    # rows longer than the peeled schedule takes
+    ((5, 1500), (2, 40)),
+    ((4, 6, 1100), (3, 2, 9)),
 ]
 
 
