@@ -5,7 +5,6 @@
 #include <atomic>
 #include <map>
 #include <mutex>
-#include <cstdlib>
 #include <utility>
 #include <vector>
 
@@ -128,12 +127,19 @@ static const exsum::Aux *aux_for(void *stream)
         cudaGetLastError();
         return nullptr;
     }
+    // The side branches are chains of short kernels on the critical path,
+    // launched while the caller's stream runs a full-tensor pass: the highest
+    // stream priority lets their blocks take SM slots as the pass's blocks
+    // retire.  (Graphs keep it per node; cudaGraphInstantiateFlagUseNodePriority
+    // honours it, see exsum_graph_instantiate.)
     exsum::Aux a;
     int lo = 0, hi = 0;
-    cudaDeviceGetStreamPriorityRange(&lo, &hi);
-    int prio = getenv("EXSUM_EXP_PRIO") ? hi : 0;
-    if (cudaStreamCreateWithPriority(&a.side, cudaStreamNonBlocking, prio) != cudaSuccess ||
-        cudaStreamCreateWithPriority(&a.side2, cudaStreamNonBlocking, prio) != cudaSuccess ||
+    if (cudaDeviceGetStreamPriorityRange(&lo, &hi) != cudaSuccess) {
+        cudaGetLastError();
+        hi = 0;
+    }
+    if (cudaStreamCreateWithPriority(&a.side, cudaStreamNonBlocking, hi) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&a.side2, cudaStreamNonBlocking, hi) != cudaSuccess ||
         cudaEventCreateWithFlags(&a.fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&a.join, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&a.fork2, cudaEventDisableTiming) != cudaSuccess ||

@@ -72,6 +72,7 @@ k_row_totals(const SIn *__restrict__ X, typename M::car_t *__restrict__ R, int64
 {
     using Lt = typename M::loc_t;
     constexpr int RPW = 32 / LPR;
+    constexpr int RU = 4;  // row groups in flight per warp
     const int lane = threadIdx.x & 31;
     const int sub = lane & (LPR - 1);
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -79,28 +80,51 @@ k_row_totals(const SIn *__restrict__ X, typename M::car_t *__restrict__ R, int64
     const uint64_t pol = l2_policy_evict_last();  // the first pass reads X too
     constexpr size_t VALIGN = sizeof(SIn) * 4 >= 16 ? 16 : sizeof(SIn) * 4;
     const bool vec = (L % 4 == 0) && ((((uintptr_t)X) & (VALIGN - 1)) == 0);
-    const SIn *src = X + (warp * RPW + lane / LPR) * (int64_t)L + 4 * sub;
-    const int64_t step = nwarps * RPW * (int64_t)L;
-    for (int64_t r = warp * RPW + lane / LPR; r - lane / LPR < rows; r += nwarps * RPW, src += step) {
-        Lt acc = M::lid();
-        if (r < rows) {
-            if (vec) {
-                for (int c = 4 * sub; c < L; c += 4 * LPR) {
-                    Lt v[4];
-                    load4<M>(src + (c - 4 * sub), true, 4, v, pol);
-                    acc = M::lop(acc, M::lop(M::lop(v[0], v[1]), M::lop(v[2], v[3])));
-                }
-            } else {
-                for (int c = 4 * sub; c < L; c += 4 * LPR) {
-                    Lt v[4];
-                    load4<M>(src + (c - 4 * sub), false, min(4, L - c), v, pol);
-                    acc = M::lop(acc, M::lop(M::lop(v[0], v[1]), M::lop(v[2], v[3])));
-                }
+    constexpr int SPAN = 4 * LPR;  // elements one pass over the lanes covers
+    for (int64_t rb = warp * (RPW * RU); rb < rows; rb += nwarps * (RPW * RU)) {
+        Lt acc[RU];
+        const SIn *src[RU];
+#pragma unroll
+        for (int u = 0; u < RU; ++u) {
+            int64_t r = rb + u * RPW + lane / LPR;
+            if (r >= rows) r = rows - 1;  // a valid row; its total is not stored
+            acc[u] = M::lid();
+            src[u] = X + r * (int64_t)L + 4 * sub;
+        }
+        int c = 4 * sub;
+        // two vectors of every row per iteration, all loads issued first
+        for (; c + SPAN < L; c += 2 * SPAN) {
+            const bool f0 = vec, f1 = vec && c + SPAN + 4 <= L;
+            const int v1 = min(4, L - c - SPAN);
+            Lt w[RU][8];
+#pragma unroll
+            for (int u = 0; u < RU; ++u) {
+                load4<M>(src[u], f0, 4, w[u], pol);
+                load4<M>(src[u] + SPAN, f1, v1, w[u] + 4, pol);
+                src[u] += 2 * SPAN;
             }
+#pragma unroll
+            for (int u = 0; u < RU; ++u)
+                acc[u] = M::lop(acc[u], M::lop(M::lop(M::lop(w[u][0], w[u][1]), M::lop(w[u][2], w[u][3])),
+                                               M::lop(M::lop(w[u][4], w[u][5]), M::lop(w[u][6], w[u][7]))));
+        }
+        if (c < L) {
+            const bool f0 = vec && c + 4 <= L;
+            const int v0 = min(4, L - c);
+            Lt w[RU][4];
+#pragma unroll
+            for (int u = 0; u < RU; ++u) load4<M>(src[u], f0, v0, w[u], pol);
+#pragma unroll
+            for (int u = 0; u < RU; ++u)
+                acc[u] = M::lop(acc[u], M::lop(M::lop(w[u][0], w[u][1]), M::lop(w[u][2], w[u][3])));
         }
 #pragma unroll
-        for (int m = LPR >> 1; m > 0; m >>= 1) acc = M::lop(acc, shfl_xor(acc, m));
-        if (sub == 0 && r < rows) R[r] = M::template put<typename M::car_t>(M::widen(acc));
+        for (int u = 0; u < RU; ++u) {
+#pragma unroll
+            for (int m = LPR >> 1; m > 0; m >>= 1) acc[u] = M::lop(acc[u], shfl_xor(acc[u], m));
+            const int64_t r = rb + u * RPW + lane / LPR;
+            if (sub == 0 && r < rows) R[r] = M::template put<typename M::car_t>(M::widen(acc[u]));
+        }
     }
 }
 
@@ -179,8 +203,8 @@ __device__ __forceinline__ void smem_walk(typename M::loc_t *col, int LS, int k,
 template <class M, class SIn, class SOut, int KMAX, int EPL>
 __global__ void __launch_bounds__(256)
 k_rowx(const SIn *__restrict__ in, const typename M::car_t *__restrict__ T,
-       SOut *__restrict__ out, int64_t O, int n2, int L, int k2, int k3, int TR, int GO,
-       int ntile, int RS, int RSA, int LS, int lpr)
+       const typename M::car_t *__restrict__ R1, int k1, SOut *__restrict__ out, int64_t O, int n2,
+       int L, int k2, int k3, int TR, int GO, int ntile, int RS, int RSA, int LS, int lpr)
 {
     using Lt = typename M::loc_t;
     using A = typename M::acc_t;
@@ -201,6 +225,9 @@ k_rowx(const SIn *__restrict__ in, const typename M::car_t *__restrict__ T,
     const uint64_t pol_in = l2_policy_evict_first();
     const uint64_t pol_out = l2_policy_evict_first();
     Lt *sbuf = tile + (int64_t)GO * RSA * LS;
+    using C = typename M::car_t;
+    C *Tt = reinterpret_cast<C *>(
+        rowx_smem + (((int64_t)GO * RSA * LS + (int64_t)(blockDim.x >> 5) * rpw * LPs) * sizeof(Lt) + 15) / 16 * 16);
 
     // identity: strip padding of the output rows, slot L of every suffix row
     const int LE = (L + EPL - 1) / EPL * EPL;
@@ -243,6 +270,29 @@ k_rowx(const SIn *__restrict__ in, const typename M::car_t *__restrict__ T,
                 }
             }
             cp_async_wait_all();
+        }
+    }
+    // One-dimensional tail (d == 2, R1 != nullptr): T[x] for the tile's rows is
+    // the excluded sum of the row totals R1 with box k1 (k1 <= 64): the totals
+    // before the tile (P0), those from the last row's box end on (S0), and the
+    // at most nout + k1 - 1 in between, staged in Tt first.
+    if (R1 && warp == 0) {
+        const int B1 = min(n2, a + nout - 1 + k1);
+        A p0 = M::id(), s0 = M::id();
+        for (int y = lane; y < a; y += 32) p0 = M::op(p0, M::get(R1[y]));
+        for (int y = B1 + lane; y < n2; y += 32) s0 = M::op(s0, M::get(R1[y]));
+        for (int y = a + lane; y < B1; y += 32) Tt[TR + (y - a)] = R1[y];
+#pragma unroll
+        for (int m = 16; m > 0; m >>= 1) {
+            p0 = M::op(p0, shfl_xor(p0, m));
+            s0 = M::op(s0, shfl_xor(s0, m));
+        }
+        __syncwarp();
+        for (int r = lane; r < nout; r += 32) {
+            A pre = p0, suf = s0;
+            for (int y = 0; y < r; ++y) pre = M::op(pre, M::get(Tt[TR + y]));
+            for (int y = r + k1; y < B1 - a; ++y) suf = M::op(suf, M::get(Tt[TR + y]));
+            Tt[r] = M::template put<C>(M::op(pre, suf));
         }
     }
     if (!staged) {
@@ -364,7 +414,7 @@ k_rowx(const SIn *__restrict__ in, const typename M::car_t *__restrict__ T,
             }
             __syncwarp();
             if (live) {
-                const A tv = M::get(T[rowbase + r]);
+                const A tv = M::get(R1 ? Tt[r] : T[rowbase + r]);
                 SOut *dst = out + (rowbase + r) * (int64_t)L + e0;
                 SOut res[EPL];
                 bool done = false;

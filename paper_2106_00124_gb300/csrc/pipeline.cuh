@@ -310,6 +310,7 @@ struct Pipe {
     // so this needs no carries; the window along dimension d-1 is fused into
     // the final pass when its tile holds enough rows.
     static constexpr int ROWX_THREADS = 256;
+    static constexpr int64_t ROWX_TAIL = 4096;  // 1-D recursion folded into the final pass
 
     struct RowPlan {
         bool ok = false, fuse = false;
@@ -383,56 +384,59 @@ struct Pipe {
         rp.LS = (int)LS;
         rp.lpr = (int)lpr;
         rp.epl = (int)epl;
-        rp.smem = (size_t)(GO * rp.RSA * LS + (ROWX_THREADS / 32) * rpw * LPs) * s;
+        rp.smem = ((size_t)(GO * rp.RSA * LS + (ROWX_THREADS / 32) * rpw * LPs) * s + 15) / 16 * 16 +
+                  (size_t)(2 * TR + 64) * sizeof(CAR);  // + T and the totals of a 1-D tail
         return rp;
     }
 
     template <class SF, class SOut, int KM, int EPL>
-    static void rowx_epl(Ctx &cx, const RowPlan &rp, const SF *src, const CAR *T, SOut *out,
-                         int64_t O2, int64_t n2, int64_t L, int kk, int k3)
+    static void rowx_epl(Ctx &cx, const RowPlan &rp, const SF *src, const CAR *T, const CAR *R1,
+                         SOut *out, int64_t O2, int64_t n2, int64_t L, int kk, int k3, int k1)
     {
         auto kern = k_rowx<M, SF, SOut, KM, EPL>;
         if (rp.smem > 48 * 1024)
             cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rp.smem);
         const unsigned blocks = (unsigned)(cdiv(O2, rp.GO) * rp.ntile);
-        kern<<<blocks, ROWX_THREADS, rp.smem, cx.stream>>>(src, T, out, O2, (int)n2, (int)L, kk, k3,
-                                                          rp.TR, rp.GO, rp.ntile, rp.RS, rp.RSA,
-                                                          rp.LS, rp.lpr);
+        kern<<<blocks, ROWX_THREADS, rp.smem, cx.stream>>>(src, T, R1, k1, out, O2, (int)n2, (int)L,
+                                                          kk, k3, rp.TR, rp.GO, rp.ntile, rp.RS,
+                                                          rp.RSA, rp.LS, rp.lpr);
     }
 
     template <class SF, class SOut, int KM>
-    static void rowx_go(Ctx &cx, const RowPlan &rp, const SF *src, const CAR *T, SOut *out,
-                        int64_t O2, int64_t n2, int64_t L, int kk, int k3)
+    static void rowx_go(Ctx &cx, const RowPlan &rp, const SF *src, const CAR *T, const CAR *R1, SOut *out,
+                        int64_t O2, int64_t n2, int64_t L, int kk, int k3, int k1)
     {
         if (rp.epl == 4)
-            rowx_epl<SF, SOut, KM, 4>(cx, rp, src, T, out, O2, n2, L, kk, k3);
+            rowx_epl<SF, SOut, KM, 4>(cx, rp, src, T, R1, out, O2, n2, L, kk, k3, k1);
         else if (rp.epl == 8)
-            rowx_epl<SF, SOut, KM, 8>(cx, rp, src, T, out, O2, n2, L, kk, k3);
+            rowx_epl<SF, SOut, KM, 8>(cx, rp, src, T, R1, out, O2, n2, L, kk, k3, k1);
         else if (rp.epl == 16)
-            rowx_epl<SF, SOut, KM, 16>(cx, rp, src, T, out, O2, n2, L, kk, k3);
+            rowx_epl<SF, SOut, KM, 16>(cx, rp, src, T, R1, out, O2, n2, L, kk, k3, k1);
         else if (rp.epl == 32 && sizeof(L_) == 4)
-            rowx_epl<SF, SOut, KM, (sizeof(L_) == 4 ? 32 : 16)>(cx, rp, src, T, out, O2, n2, L, kk, k3);
+            rowx_epl<SF, SOut, KM, (sizeof(L_) == 4 ? 32 : 16)>(cx, rp, src, T, R1, out, O2, n2, L, kk, k3, k1);
         else if (cx.status == ST_OK)
             cx.status = ST_EUNSUP;  // not reachable: row_plan gives one of the widths above
     }
 
     template <class SF, class SOut>
-    static void rowx_launch(Ctx &cx, const RowPlan &rp, const SF *src, const CAR *T, SOut *out,
+    static void rowx_launch(Ctx &cx, const RowPlan &rp, const SF *src, const CAR *T, const CAR *R1, SOut *out,
                             int64_t O2, int64_t n2, int64_t L, int64_t k2, int64_t k3)
     {
         if (cx.dry || !cx.ok()) return;
+        // the 1-D tail (d == 2) is the excluded sum of R along n2 with box k2
+        const int k1 = R1 ? (int)k2 : 0;
         cx.before(TAG_ROWX, O2 * n2 * L);
         const int kk = rp.fuse ? (int)k2 : 1;
         if (!rp.fuse)
-            rowx_go<SF, SOut, 1>(cx, rp, src, T, out, O2, n2, L, 1, (int)k3);
+            rowx_go<SF, SOut, 1>(cx, rp, src, T, R1, out, O2, n2, L, 1, (int)k3, k1);
         else if (kk <= 4)
-            rowx_go<SF, SOut, 4>(cx, rp, src, T, out, O2, n2, L, kk, (int)k3);
+            rowx_go<SF, SOut, 4>(cx, rp, src, T, R1, out, O2, n2, L, kk, (int)k3, k1);
         else if (kk <= 8)
-            rowx_go<SF, SOut, 8>(cx, rp, src, T, out, O2, n2, L, kk, (int)k3);
+            rowx_go<SF, SOut, 8>(cx, rp, src, T, R1, out, O2, n2, L, kk, (int)k3, k1);
         else if (kk <= 16)
-            rowx_go<SF, SOut, 16>(cx, rp, src, T, out, O2, n2, L, kk, (int)k3);
+            rowx_go<SF, SOut, 16>(cx, rp, src, T, R1, out, O2, n2, L, kk, (int)k3, k1);
         else
-            rowx_go<SF, SOut, 32>(cx, rp, src, T, out, O2, n2, L, kk, (int)k3);
+            rowx_go<SF, SOut, 32>(cx, rp, src, T, R1, out, O2, n2, L, kk, (int)k3, k1);
         cx.check_launch();
     }
 
@@ -456,7 +460,10 @@ struct Pipe {
         CAR *R = cx.take<CAR>(rows);
         CAR *T = cx.take<CAR>(rows);
         // Row totals and the lower-dimensional recursion run on the side
-        // stream while the BDBS passes run on the caller's.
+        // stream while the BDBS passes run on the caller's.  A one-dimensional
+        // recursion of at most ROWX_TAIL elements is left to the final pass
+        // (it needs only R).
+        const bool tail = d == 2 && n[0] <= ROWX_TAIL && k[0] <= 64;
         const Aux *aux = cx.aux;
         const bool fork = P > 0 && aux && aux->side && !cx.dry && cx.ok();
         cudaStream_t main_stream = cx.stream;
@@ -469,7 +476,7 @@ struct Pipe {
         if (!cx.dry && cx.ok()) {
             cx.before(TAG_ROWSUM, N);
             const int lpr = row_lanes(L);
-            int64_t blocks = cdiv(rows, 8 * (32 / lpr));
+            int64_t blocks = cdiv(rows, 8 * 4 * (32 / lpr));
             if (blocks > 152 * 8) blocks = 152 * 8;
             if (lpr <= 4)
                 k_row_totals<M, SIn, 4><<<(unsigned)blocks, 256, 0, cx.stream>>>(X, R, rows, (int)L);
@@ -481,9 +488,11 @@ struct Pipe {
                 k_row_totals<M, SIn, 32><<<(unsigned)blocks, 256, 0, cx.stream>>>(X, R, rows, (int)L);
             cx.check_launch();
         }
-        cx.level++;
-        Pipe<MC>::template excluded<CAR, CAR>(cx, R, T, d - 1, n, k);
-        cx.level--;
+        if (!tail) {
+            cx.level++;
+            Pipe<MC>::template excluded<CAR, CAR>(cx, R, T, d - 1, n, k);
+            cx.level--;
+        }
         cx.aux = aux;
         if (fork) {
             cudaEventRecord(aux->join, aux->side);
@@ -503,10 +512,11 @@ struct Pipe {
             cur = dst;
         }
         if (fork) cudaStreamWaitEvent(main_stream, aux->join, 0);
+        const CAR *R1 = tail ? R : nullptr;
         if (P > 0)
-            rowx_launch<SOut, SOut>(cx, rp, (const SOut *)cur, T, out, O2, n2, L, k[d - 2], k[d - 1]);
+            rowx_launch<SOut, SOut>(cx, rp, (const SOut *)cur, T, R1, out, O2, n2, L, k[d - 2], k[d - 1]);
         else
-            rowx_launch<SIn, SOut>(cx, rp, (const SIn *)cur, T, out, O2, n2, L, k[d - 2], k[d - 1]);
+            rowx_launch<SIn, SOut>(cx, rp, (const SIn *)cur, T, R1, out, O2, n2, L, k[d - 2], k[d - 1]);
     }
 
     // ---- excluded sums: box-complement, one dimension-reduction step per level ---------------
