@@ -9,8 +9,10 @@ line (rank 0).
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
   python bench.py --impl reference ...   # the CPU oracle, timed on host cores
 
-Timing: the step is captured once into a CUDA graph; each replay is
-bracketed by CUDA events on the stream it runs on, and between steps a
+Timing: the step is captured once into a CUDA graph, instantiated by the
+library so that the side branches keep their stream priority
+(exsum_graph_instantiate); each launch of it is bracketed by CUDA events
+on the stream it runs on, and between steps a
 256 MiB buffer is written to flush the 129 MB L2, outside the timed spans.
 `value` sums the K step spans.  The per-kernel roofline comes from a second
 capture of the same step with the library's launch trace on (event-record
@@ -250,21 +252,24 @@ def run_ours(args):
         step(cap_stream.cuda_stream)
     cap_stream.synchronize()
 
+    # The graph is instantiated by the library (exsum_graph_instantiate), which
+    # keeps the per-node stream priorities of the side branches.
     def capture(traced):
-        g = torch.cuda.CUDAGraph()
+        g = torch.cuda.CUDAGraph(keep_graph=True)
         ex.exsum_trace_collect(clear=True)
         ex.exsum_trace_enable(traced)
         l0 = ex.exsum_launch_count()
         with torch.cuda.graph(g, stream=cap_stream):
             step(cap_stream.cuda_stream)
         ex.exsum_trace_enable(False)
-        return g, ex.exsum_launch_count() - l0
+        return g, ex.exsum_graph_instantiate(g.raw_cuda_graph()), ex.exsum_launch_count() - l0
 
-    graph, launches_per_step = capture(False)
-    tgraph, _ = capture(True)
+    graph, gexec, launches_per_step = capture(False)
+    tgraph, tgexec, _ = capture(True)
+    sh = stream.cuda_stream
     for _ in range(args.warmup):
         flush.fill_(1)
-        graph.replay()
+        ex.exsum_graph_launch(gexec, sh)
     torch.cuda.synchronize()
 
     # ---- timed region -----------------------------------------------------------------------
@@ -278,14 +283,14 @@ def run_ours(args):
     for i in range(args.steps):
         flush.fill_(1)
         evs[i][0].record(stream)
-        graph.replay()
+        ex.exsum_graph_launch(gexec, sh)
         evs[i][1].record(stream)
     torch.cuda.synchronize()
     # Per-kernel durations: the traced graph over the same number of steps.
     trace = []  # (position of the launch in the step, kernel, level, elements, ms)
     for i in range(args.steps):
         flush.fill_(1)
-        tgraph.replay()
+        ex.exsum_graph_launch(tgexec, sh)
         torch.cuda.synchronize()
         trace.extend((j,) + rec for j, rec in enumerate(ex.exsum_trace_collect(cap=256, clear=False)))
     launches = launches_per_step * args.steps
@@ -293,6 +298,9 @@ def run_ours(args):
         torch.distributed.barrier()
     clk = clocks.stop()
     ex.exsum_trace_collect(clear=True)
+    ex.exsum_graph_exec_destroy(gexec)
+    ex.exsum_graph_exec_destroy(tgexec)
+    del graph, tgraph
     step_ms = [a.elapsed_time(b) for a, b in evs]
     total_s = sum(step_ms) / 1e3
     max_s = max_over_ranks(total_s, world, device)

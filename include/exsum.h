@@ -301,6 +301,27 @@ const char *exsum_kernel_name(int tag);
 /* Kernels launched by the library in this process so far. */
 int64_t exsum_launch_count(void);
 
+/*
+ * Graph helpers (no counterpart in the paper).  Calls captured into a CUDA
+ * graph from the caller's stream keep, per kernel node, the priority of the
+ * stream it was captured on: the side branches of excluded sums run on
+ * streams of the greatest priority.  A graph instantiated here honours those
+ * node priorities (cudaGraphInstantiateFlagUseNodePriority), so the short
+ * side-branch kernels are not queued behind the blocks of the full-tensor
+ * pass they run beside; a graph instantiated without the flag runs every
+ * node at the priority of the stream it is launched into.
+ *
+ * `graph` is a cudaGraph_t (the caller keeps ownership); *exec receives a
+ * cudaGraphExec_t that the caller frees with exsum_graph_exec_destroy.
+ * exsum_graph_launch launches it into `stream` (a cudaStream_t, NULL for the
+ * legacy default stream) and returns without waiting.  All three return
+ * EXSUM_OK, EXSUM_EINVAL for a NULL graph, exec or exec pointer, or
+ * EXSUM_ECUDA (see exsum_last_cuda_error).
+ */
+int exsum_graph_instantiate(void *graph, void **exec);
+int exsum_graph_launch(void *exec, void *stream);
+int exsum_graph_exec_destroy(void *exec);
+
 #ifdef __cplusplus
 }
 #endif

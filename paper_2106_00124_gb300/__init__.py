@@ -94,6 +94,9 @@ _SIG = {
                              ctypes.c_int, ctypes.c_int], ctypes.c_int),
     "exsum_kernel_name": ([ctypes.c_int], ctypes.c_char_p),
     "exsum_launch_count": ([], ctypes.c_int64),
+    "exsum_graph_instantiate": ([_P, ctypes.POINTER(_P)], ctypes.c_int),
+    "exsum_graph_launch": ([_P, _P], ctypes.c_int),
+    "exsum_graph_exec_destroy": ([_P], ctypes.c_int),
     "exsum_batch_create": ([ctypes.POINTER(exsum_desc), ctypes.c_int, ctypes.c_int, _P,
                             ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
     "exsum_batch_launch": ([_P, _P], ctypes.c_int),
@@ -232,6 +235,29 @@ def exsum_kernel_name(tag):
 
 def exsum_launch_count():
     return int(_load().exsum_launch_count())
+
+
+def exsum_graph_instantiate(graph):
+    """Instantiates a captured cudaGraph_t (an integer handle, e.g.
+    torch.cuda.CUDAGraph(keep_graph=True).raw_cuda_graph()) with per-node
+    priorities honoured; returns the cudaGraphExec_t handle."""
+    ex = _P()
+    rc = _load().exsum_graph_instantiate(_P(int(graph)), ctypes.byref(ex))
+    if rc != EXSUM_OK:
+        raise ExsumError(rc, "exsum_graph_instantiate")
+    return int(ex.value)
+
+
+def exsum_graph_launch(exec_, stream=0):
+    rc = _load().exsum_graph_launch(_P(int(exec_)), _P(int(stream)))
+    if rc != EXSUM_OK:
+        raise ExsumError(rc, "exsum_graph_launch")
+
+
+def exsum_graph_exec_destroy(exec_):
+    rc = _load().exsum_graph_exec_destroy(_P(int(exec_)))
+    if rc != EXSUM_OK:
+        raise ExsumError(rc, "exsum_graph_exec_destroy")
 
 
 def exsum_batch_create(descs, lanes=0, stream=0):

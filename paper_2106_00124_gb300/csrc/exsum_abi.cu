@@ -375,6 +375,46 @@ const char *exsum_kernel_name(int tag)
 
 int64_t exsum_launch_count(void) { return g_launches.load(); }
 
+int exsum_graph_instantiate(void *graph, void **exec)
+{
+    if (!graph || !exec) return EXSUM_EINVAL;
+    cudaGraphExec_t e = nullptr;
+    const cudaError_t ce = cudaGraphInstantiateWithFlags(&e, (cudaGraph_t)graph,
+                                                         cudaGraphInstantiateFlagUseNodePriority);
+    if (ce != cudaSuccess) {
+        g_last_cuda_error = (int)ce;
+        cudaGetLastError();
+        *exec = nullptr;
+        return EXSUM_ECUDA;
+    }
+    *exec = (void *)e;
+    return EXSUM_OK;
+}
+
+int exsum_graph_launch(void *exec, void *stream)
+{
+    if (!exec) return EXSUM_EINVAL;
+    const cudaError_t ce = cudaGraphLaunch((cudaGraphExec_t)exec, (cudaStream_t)stream);
+    if (ce != cudaSuccess) {
+        g_last_cuda_error = (int)ce;
+        cudaGetLastError();
+        return EXSUM_ECUDA;
+    }
+    return EXSUM_OK;
+}
+
+int exsum_graph_exec_destroy(void *exec)
+{
+    if (!exec) return EXSUM_EINVAL;
+    const cudaError_t ce = cudaGraphExecDestroy((cudaGraphExec_t)exec);
+    if (ce != cudaSuccess) {
+        g_last_cuda_error = (int)ce;
+        cudaGetLastError();
+        return EXSUM_ECUDA;
+    }
+    return EXSUM_OK;
+}
+
 }  // extern "C"
 
 namespace exsum {

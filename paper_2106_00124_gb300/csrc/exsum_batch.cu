@@ -209,7 +209,8 @@ int build(exsum_batch *p)
     if (rc) return rc;
     if (e != cudaSuccess) return EXSUM_ECUDA;
     p->kernels = exsum_launch_count() - launches0;
-    e = cudaGraphInstantiate(&p->exec, p->graph, 0);
+    // honour the per-node priorities of the side branches (see exsum_graph_instantiate)
+    e = cudaGraphInstantiateWithFlags(&p->exec, p->graph, cudaGraphInstantiateFlagUseNodePriority);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return EXSUM_ECUDA;

@@ -53,6 +53,10 @@ CASES = [
     ((20, 50), (4, 1)),
     ((3, 4, 5, 40), (2, 3, 4, 7)),
     ((4, 5, 64), (1, 1, 8)),
+    # the lower-dimensional problem one-dimensional but too long (or its box
+    # too wide) to fold into the final pass
+    ((5000, 20), (3, 4)),
+    ((300, 40), (100, 5)),
     # rows longer than the peeled schedule takes
     ((5, 1500), (2, 40)),
     ((4, 6, 1100), (3, 2, 9)),
