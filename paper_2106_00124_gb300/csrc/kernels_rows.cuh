@@ -272,11 +272,18 @@ k_rowx(const SIn *__restrict__ in, const typename M::car_t *__restrict__ T,
             cp_async_wait_all();
         }
     }
-    // One-dimensional tail (d == 2, R1 != nullptr): T[x] for the tile's rows is
-    // the excluded sum of the row totals R1 with box k1 (k1 <= 64): the totals
-    // before the tile (P0), those from the last row's box end on (S0), and the
-    // at most nout + k1 - 1 in between, staged in Tt first.
-    if (R1 && warp == 0) {
+    // T of the tile's rows, into shared memory while the tile is in flight.
+    // One-dimensional tail (d == 2, R1 != nullptr): T[x] is the excluded sum
+    // of the row totals R1 with box k1 (k1 <= 64), from the totals before the
+    // tile (P0), those from the last row's box end on (S0), and the at most
+    // nout + k1 - 1 in between, staged in Tt first.
+    if (!R1) {
+        for (int i = threadIdx.x; i < ng * nout; i += blockDim.x) {
+            const int g = i / nout;
+            const int r = i - g * nout;
+            Tt[g * TR + r] = T[(o0 + g) * n2 + a + r];
+        }
+    } else if (warp == 0) {
         const int B1 = min(n2, a + nout - 1 + k1);
         A p0 = M::id(), s0 = M::id();
         for (int y = lane; y < a; y += 32) p0 = M::op(p0, M::get(R1[y]));
@@ -414,7 +421,7 @@ k_rowx(const SIn *__restrict__ in, const typename M::car_t *__restrict__ T,
             }
             __syncwarp();
             if (live) {
-                const A tv = M::get(R1 ? Tt[r] : T[rowbase + r]);
+                const A tv = M::get(Tt[g * TR + r]);
                 SOut *dst = out + (rowbase + r) * (int64_t)L + e0;
                 SOut res[EPL];
                 bool done = false;

@@ -385,7 +385,7 @@ struct Pipe {
         rp.lpr = (int)lpr;
         rp.epl = (int)epl;
         rp.smem = ((size_t)(GO * rp.RSA * LS + (ROWX_THREADS / 32) * rpw * LPs) * s + 15) / 16 * 16 +
-                  (size_t)(2 * TR + 64) * sizeof(CAR);  // + T and the totals of a 1-D tail
+                  (size_t)((GO * TR > 2 * TR + 64) ? GO * TR : 2 * TR + 64) * sizeof(CAR);  // + the tile's T (and a 1-D tail's totals)
         return rp;
     }
 
