@@ -382,16 +382,22 @@ k_rowx(const SIn *__restrict__ in, const typename M::car_t *__restrict__ T,
 #pragma unroll
                 for (int j = 0; j < EPL; ++j) t = M::lop(t, v[j]);
             }
-            // segmented inclusive scans of the strip totals, forwards and backwards
+            // segmented inclusive scans of the strip totals, forwards and
+            // backwards: full-warp shuffles, the lane tests keep each scan
+            // inside its lpr-lane segment
             Lt pre = t, suf = t;
-            for (int dl = 1; dl < lpr; dl <<= 1) {
-                const Lt u = shfl_up_w(pre, dl, lpr);
-                const Lt w = shfl_down_w(suf, dl, lpr);
-                if (sub >= dl) pre = M::lop(u, pre);
-                if (sub + dl < lpr) suf = M::lop(suf, w);
+#pragma unroll
+            for (int lv = 0; lv < 5; ++lv) {
+                const int dl = 1 << lv;
+                if (dl < lpr) {
+                    const Lt u = shfl_up(pre, dl);
+                    const Lt w = shfl_down(suf, dl);
+                    if (sub >= dl) pre = M::lop(u, pre);
+                    if (sub + dl < lpr) suf = M::lop(suf, w);
+                }
             }
-            Lt p = shfl_up_w(pre, 1, lpr);
-            Lt s = shfl_down_w(suf, 1, lpr);
+            Lt p = shfl_up(pre, 1);
+            Lt s = shfl_down(suf, 1);
             if (sub == 0) p = M::lid();
             if (sub == lpr - 1) s = M::lid();
             if (live) {
