@@ -76,6 +76,82 @@ __device__ __forceinline__ void store4(SOut *p, bool vec, int valid, const typen
     }
 }
 
+// ---------------------------------------------------------------------------
+// BDBS-Along-Dim along a strided dimension (view [O, n, I], I % 4 == 0,
+// 16-byte aligned rows): as k_inc_strided, but each thread walks four
+// adjacent inner positions at once with 16-byte (8-byte for bf16) loads and
+// stores -- the register BDBS walk of bdbs_walk on four columns.
+// ---------------------------------------------------------------------------
+template <class M, class SIn, class SOut, int KMAX>
+__global__ void __launch_bounds__(128)
+k_inc_strided4(const SIn *__restrict__ in, SOut *__restrict__ out, int64_t O, int n, int64_t I,
+               int k, int Lc, int nchunks)
+{
+    using Lt = typename M::loc_t;
+    const int64_t I4 = I >> 2;
+    const int64_t total = O * nchunks * I4;
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= total) return;
+    const int64_t i4 = gid % I4;
+    const int64_t rest = gid / I4;
+    const int ch = (int)(rest % nchunks);
+    const int64_t o = rest / nchunks;
+    const SIn *src = in + o * n * I + 4 * i4;
+    SOut *dst = out + o * n * I + 4 * i4;
+    const int r0 = ch * Lc;
+    const int rend = min(r0 + Lc, n);
+    const uint64_t pol_in = l2_policy_evict_first();
+    const uint64_t pol_out = l2_policy_evict_last();
+    Lt S[KMAX][4], v[KMAX][4];
+#pragma unroll
+    for (int j = 0; j < KMAX; ++j) {
+        if (j < k && r0 + j < n) {
+            load4<M>(src + (int64_t)(r0 + j) * I, true, 4, v[j], pol_in);
+        } else {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) v[j][c] = M::lid();
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) S[KMAX - 1][c] = v[KMAX - 1][c];
+#pragma unroll
+    for (int j = KMAX - 2; j >= 0; --j)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) S[j][c] = M::lop(v[j][c], S[j + 1][c]);
+    for (int sb = r0; sb < rend; sb += k) {
+        store4<M>(dst + (int64_t)sb * I, true, 4, S[0], pol_out);
+        const int nb = sb + k;
+#pragma unroll
+        for (int j = 0; j < KMAX; ++j) {
+            if (j < k && nb + j < n) {
+                load4<M>(src + (int64_t)(nb + j) * I, true, 4, v[j], pol_in);
+            } else {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) v[j][c] = M::lid();
+            }
+        }
+        Lt p[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) p[c] = M::lid();
+#pragma unroll
+        for (int j = 0; j + 1 < KMAX; ++j) {
+            Lt w[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                p[c] = M::lop(p[c], v[j][c]);
+                w[c] = M::lop(S[j + 1][c], p[c]);
+            }
+            if (j + 1 < k && sb + 1 + j < rend) store4<M>(dst + (int64_t)(sb + 1 + j) * I, true, 4, w, pol_out);
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) S[KMAX - 1][c] = v[KMAX - 1][c];
+#pragma unroll
+        for (int j = KMAX - 2; j >= 0; --j)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) S[j][c] = M::lop(v[j][c], S[j + 1][c]);
+    }
+}
+
 __device__ __forceinline__ void cp_async_wait_all()
 {
     asm volatile("cp.async.commit_group;\n" ::);

@@ -127,6 +127,23 @@ struct Pipe {
                 src, dst, N, pn1, M1, n, (int)k, nq, Rsum, Rtail, r_tail);
             cx.check_launch();
         } else {
+            if constexpr (KMAX <= 8 && sizeof(L_) == 4 && sizeof(SOut) == 4) {
+                if ((I & 3) == 0 && (((uintptr_t)src) & (sizeof(SIn) * 4 - 1)) == 0 &&
+                    (((uintptr_t)dst) & 15) == 0) {
+                    // Four inner positions per thread, 16-byte accesses;
+                    // chunks short enough for ~1024 threads per SM.
+                    int Lc = 128;
+                    while (Lc > 2 * k && Lc > 16 && O * cdiv(n, Lc) * (I / 4) < 152 * 1024) Lc >>= 1;
+                    if (Lc > n) Lc = (int)n;
+                    const int nchunks = (int)cdiv(n, Lc);
+                    const int64_t total = O * nchunks * (I / 4);
+                    cx.before(TAG_INC_STRIDED, O * n * I);
+                    k_inc_strided4<M, SIn, SOut, KMAX><<<(unsigned)cdiv(total, 128), 128, 0, cx.stream>>>(
+                        src, dst, O, (int)n, I, (int)k, Lc, nchunks);
+                    cx.check_launch();
+                    return;
+                }
+            }
             // Chunks short enough for ~2048 threads per SM (walks of a few blocks).
             int Lc = 128;
             while (Lc > 2 * k && Lc > 16 && O * cdiv(n, Lc) * I < 152 * 2048) Lc >>= 1;
