@@ -372,24 +372,35 @@ struct Pipe {
         const int64_t groups = cdiv(O2, GO);
         // rows per tile for at least two blocks per SM, when the tensor has them
         const int64_t tr_par = groups >= 2 * 152 ? n2 : cdiv(n2, cdiv(2 * 152, groups));
+        // rows a tile holds: TR, the k2 - 1 halo rows and the identity rows the
+        // column walk may read past them
+        auto rows_held = [&](int64_t tr, bool f) -> int64_t {
+            return f ? (tr - 1) / k2 * k2 + 2 * k2 : tr;
+        };
         auto fit = [&](int64_t budget, bool f, int64_t &TR, int64_t &ntile) -> bool {
-            // rows held: the tile, k2 - 1 halo rows and the identity rows the
-            // column walk may read past them (at most 2 k2 rows past the tile)
-            int64_t trmax = budget / (GO * LS * s) - (f ? 2 * k2 : 0);
-            int64_t cap = f ? (tr_par > 2 * k2 ? tr_par : 2 * k2) : tr_par;
-            if (cap > 64) cap = 64;
-            if (trmax > cap) trmax = cap;
-            if (trmax >= 16) trmax &= ~(int64_t)7;
-            if (trmax < 1) return false;
-            ntile = cdiv(n2, trmax);
+            int64_t tr = f ? (tr_par > 2 * k2 ? tr_par : 2 * k2) : tr_par;
+            if (tr > 64) tr = 64;
+            while (tr >= 1 && rows_held(tr, f) * GO * LS * s > budget) --tr;
+            if (tr < 1) return false;
+            if (tr >= 16) tr &= ~(int64_t)7;
+            ntile = cdiv(n2, tr);
             TR = cdiv(n2, ntile);
             return !f || ntile == 1 || TR >= 2 * k2;
         };
         int64_t TR = 1, ntile = 1;
         bool fuse = false;
-        if (k2 > 1 && k2 <= 32)
-            fuse = fit(48 * 1024, true, TR, ntile) || fit(100 * 1024, true, TR, ntile);
-        if (!fuse && !fit(44 * 1024, false, TR, ntile)) return rp;
+        // Four blocks per SM (228 KB, 1 KB reserved per block, less the
+        // suffix rows and T) when that still gives tiles of at least 32 rows
+        // or whole slices; otherwise the tallest tile (at most 64 rows) two
+        // blocks per SM allow, so that the halo rows stay a small part of
+        // what a block stages.
+        const int64_t extra = (int64_t)(ROWX_THREADS / 32) * rpw * LPs * s + 2 * 64 * 16 + 64 * 16;
+        const int64_t four = 56 * 1024 - extra, two = 113 * 1024 - extra;
+        if (k2 > 1 && k2 <= 32) {
+            fuse = fit(four, true, TR, ntile) && (ntile == 1 || TR >= 32);
+            if (!fuse) fuse = fit(two, true, TR, ntile);
+        }
+        if (!fuse && !fit(four, false, TR, ntile)) return rp;
         if (groups * ntile >= (1ll << 31)) return rp;
         rp.ok = true;
         rp.fuse = fuse;
@@ -397,7 +408,7 @@ struct Pipe {
         rp.TR = (int)TR;
         rp.ntile = (int)ntile;
         rp.RS = (int)(fuse ? TR + k2 - 1 : TR);
-        rp.RSA = (int)(fuse ? (TR - 1) / k2 * k2 + 2 * k2 : TR);
+        rp.RSA = (int)rows_held(TR, fuse);
         rp.LS = (int)LS;
         rp.lpr = (int)lpr;
         rp.epl = (int)epl;
