@@ -77,155 +77,6 @@ k_inc_strided(const SIn *__restrict__ in, SOut *__restrict__ out, int64_t O, int
 }
 
 // ---------------------------------------------------------------------------
-// BDBS-Along-Dim along the contiguous dimension (rows of length n).  A block
-// takes ROWS "virtual rows" (row, chunk of Lc outputs), stages each with its
-// k-1 halo into a padded shared-memory tile with coalesced, batched loads,
-// lets one thread walk each virtual row from shared memory (odd row stride:
-// the threads of a warp hit distinct banks), writes results back in place
-// and stores them coalesced.
-//
-// With Rsum != nullptr the block also produces the dimension-1 segment
-// totals of its input that box-complement's carries need: its virtual rows
-// are then taken as groups of 32 consecutive dimension-1 coordinates (one
-// segment) of the same (row-within-slice, chunk), and for every staged core
-// position it reduces the group over dimension 1 -- Rsum[s][c] over the
-// whole segment and Rtail[s][c] over the segment's rows from offset r_tail
-// -- from the tile it has already loaded.  Rows are x1 * R1 + rr.
-// ---------------------------------------------------------------------------
-template <class M, class SIn, class SOut, int KMAX, int ROWS>
-__global__ void __launch_bounds__(ROWS)
-k_inc_contig(const SIn *__restrict__ in, SOut *__restrict__ out, int64_t nrows, int n, int k,
-             int Lc, int nchunks, int W, uint32_t wl_magic, int WL, int64_t n1, int64_t R1,
-             typename M::car_t *__restrict__ Rsum, typename M::car_t *__restrict__ Rtail,
-             int r_tail)
-{
-    using Lt = typename M::loc_t;
-    using C = typename M::car_t;
-    constexpr int SEG = 32;
-    constexpr int UNR = 16;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    Lt *tile = reinterpret_cast<Lt *>(smem_raw);
-    __shared__ int64_t row_off[ROWS];   // global offset of position p0 of each tile row
-    __shared__ int row_lim[ROWS];       // positions of the tile row that exist (n - p0)
-    const int tid = threadIdx.x;
-    const bool sums = Rsum != nullptr;
-    {
-        int64_t off = 0;
-        int lim = 0;
-        if (!sums) {
-            const int64_t vr = (int64_t)blockIdx.x * ROWS + tid;
-            if (vr < nrows * nchunks) {
-                const int64_t row = vr / nchunks;
-                const int p0 = (int)(vr - row * nchunks) * Lc;
-                off = row * n + p0;
-                lim = n - p0;
-            }
-        } else {
-            // group = (segment, row-within-slice, chunk); SEG rows of dimension 1 per group
-            const int64_t grp = (int64_t)blockIdx.x * (ROWS / SEG) + tid / SEG;
-            const int64_t per_seg = R1 * nchunks;
-            const int64_t s = grp / per_seg;
-            const int64_t rem = grp - s * per_seg;
-            const int64_t rr = rem / nchunks;
-            const int ch = (int)(rem - rr * nchunks);
-            const int64_t x1 = s * SEG + (tid % SEG);
-            if (x1 < n1 && rr < R1) {
-                off = (x1 * R1 + rr) * n + (int64_t)ch * Lc;
-                lim = n - ch * Lc;
-            }
-        }
-        row_off[tid] = off;
-        row_lim[tid] = lim;
-    }
-    __syncthreads();
-    // Stage: tile row r holds positions p0 .. p0+WL-1 of its row (e past n).
-    if constexpr (std::is_same<SIn, Lt>::value && (sizeof(Lt) == 4 || sizeof(Lt) == 8)) {
-        // Same element type in global and shared memory: asynchronous copies,
-        // all of the block's loads in flight at once.
-        for (int e = tid; e < ROWS * WL; e += ROWS) {
-            const int r = (int)__umulhi((uint32_t)e, wl_magic);
-            const int x = e - r * WL;
-            Lt *dst = tile + r * W + x;
-            if (x < row_lim[r]) {
-                const uint32_t sdst = (uint32_t)__cvta_generic_to_shared(dst);
-                const size_t gsrc = __cvta_generic_to_global(in + row_off[r] + x);
-                if constexpr (sizeof(Lt) == 4)
-                    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sdst), "l"(gsrc));
-                else
-                    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sdst), "l"(gsrc));
-            } else {
-                *dst = M::lid();
-            }
-        }
-        asm volatile("cp.async.commit_group;\n" ::);
-        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-    } else {
-        for (int e0 = tid; e0 < ROWS * WL; e0 += ROWS * UNR) {
-            Lt vals[UNR];
-#pragma unroll
-            for (int u = 0; u < UNR; ++u) {
-                const int e = e0 + u * ROWS;
-                vals[u] = M::lid();
-                if (e < ROWS * WL) {
-                    const int r = (int)__umulhi((uint32_t)e, wl_magic);
-                    const int x = e - r * WL;
-                    if (x < row_lim[r]) vals[u] = M::lget(in[row_off[r] + x]);
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < UNR; ++u) {
-                const int e = e0 + u * ROWS;
-                if (e < ROWS * WL) {
-                    const int r = (int)__umulhi((uint32_t)e, wl_magic);
-                    tile[r * W + (e - r * WL)] = vals[u];
-                }
-            }
-        }
-    }
-    __syncthreads();
-    if (sums) {
-        // thread -> (group, core position); reduce the group's SEG rows
-        const int g = tid / SEG, x = tid % SEG;
-        const int64_t grp = (int64_t)blockIdx.x * (ROWS / SEG) + g;
-        const int64_t per_seg = R1 * nchunks;
-        const int64_t s = grp / per_seg;
-        const int64_t rem = grp - s * per_seg;
-        const int64_t rr = rem / nchunks;
-        const int ch = (int)(rem - rr * nchunks);
-        const int p = ch * Lc + x;
-        if (s * SEG < n1 && rr < R1 && x < Lc && p < n) {
-            Lt head = M::lid(), tail = M::lid();
-            const Lt *col = tile + g * SEG * W + x;
-#pragma unroll 8
-            for (int u = 0; u < SEG; ++u) {
-                const Lt v = col[u * W];
-                if (u < r_tail)
-                    head = M::lop(head, v);
-                else
-                    tail = M::lop(tail, v);
-            }
-            const int64_t c = rr * n + p;
-            const int64_t Mc = R1 * n;
-            Rsum[s * Mc + c] = M::template put<C>(M::op(M::widen(head), M::widen(tail)));
-            Rtail[s * Mc + c] = M::template put<C>(M::widen(tail));
-        }
-    }
-    {
-        const int len = min(Lc, row_lim[tid]);
-        Lt *trow = tile + tid * W;
-        bdbs_walk<M, KMAX>(
-            k, 0, len, [&](int x) { return x < WL ? trow[x] : M::lid(); },
-            [&](int x, Lt v) { trow[x] = v; });
-    }
-    __syncthreads();
-    for (int e = tid; e < ROWS * WL; e += ROWS) {
-        const int r = (int)__umulhi((uint32_t)e, wl_magic);
-        const int x = e - r * WL;
-        if (x < Lc && x < row_lim[r]) out[row_off[r] + x] = M::template lput<SOut>(tile[r * W + x]);
-    }
-}
-
-// ---------------------------------------------------------------------------
 // Rows [ya, yb) of column c of a view [*, Mc], reduced with short fp32 runs
 // (at most 32 rows) combined into the long accumulator.
 // ---------------------------------------------------------------------------

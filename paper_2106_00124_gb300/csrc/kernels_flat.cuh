@@ -1,5 +1,6 @@
-// kernels_flat.cuh -- the contiguous-dimension pass and the dimension-1 step
-// with every global access vectorised or asynchronous.
+// kernels_flat.cuh -- BDBS-Along-Dim passes with 16-byte global accesses:
+// the contiguous dimension (k_inc_flat) and four adjacent inner positions of
+// a strided dimension per thread (k_inc_strided4).
 #pragma once
 
 #include <string.h>
@@ -10,18 +11,6 @@
 
 namespace exsum {
 
-template <class T>
-__device__ __forceinline__ void cp_async_elem(T *sdst, const T *gsrc)
-{
-    const uint32_t s = (uint32_t)__cvta_generic_to_shared(sdst);
-    const size_t g = __cvta_generic_to_global(gsrc);
-    if constexpr (sizeof(T) == 4)
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(g));
-    else if constexpr (sizeof(T) == 8)
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(g));
-    else
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(g));
-}
 // Four consecutive elements starting at p (16-byte-aligned vector access when
 // `vec`, else scalar), converted to the local accumulator type.
 template <class M, class SIn>
@@ -321,54 +310,6 @@ k_inc_flat(const SIn *__restrict__ in, SOut *__restrict__ out, int64_t N, int64_
                 Rtail[s * M1 + c] = M::template put<C>(M::widen(t));
             }
         }
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Dimension-1 step (Mc > 1) with the rows staged in shared memory by
-// asynchronous copies: a block of 128 columns stages the prefix window
-// [s0, s0+L) and the target window [s0+k1, s0+k1+L) (one range when they
-// overlap), then each thread scans its column from shared memory.
-//   out[x1][c] = Q[s][c] (+) T[c] (+) (+)_{u<t} H[s0+u][c] (+) (+)_{v>=t} H[s0+k1+v][c]
-// ---------------------------------------------------------------------------
-template <class M, class SH, class SOut, int L, int NC>
-__global__ void __launch_bounds__(NC)
-k_exline_smem(const SH *__restrict__ H, const typename M::car_t *__restrict__ Q, int64_t qs,
-              const typename M::car_t *__restrict__ T, SOut *__restrict__ out, int64_t n1,
-              int64_t Mc, int64_t k1, int64_t nq)
-{
-    using Lt = typename M::loc_t;
-    // rows [0, L) prefix window; target window at tw .. tw+L
-    __shared__ SH tile[2 * L][NC];
-    const int tid = threadIdx.x;
-    const int64_t q = blockIdx.x % nq;
-    const int64_t s = blockIdx.x / nq;
-    const int64_t s0 = s * L;
-    const int64_t c = q * NC + tid;
-    const bool overlap = k1 < L;
-    const int tw = overlap ? (int)k1 : L;           // tile row of target row s0+k1
-    const int rows = overlap ? L + (int)k1 : 2 * L;
-    for (int r = 0; r < rows; ++r) {
-        const int64_t y = (overlap || r < L) ? s0 + r : s0 + k1 + (r - L);
-        if (c < Mc && y < n1) cp_async_elem(&tile[r][tid], H + y * Mc + c);
-    }
-    cp_async_wait_all();
-    if (c >= Mc) return;   // no block-wide sync after this point
-    Lt P[L];
-    Lt acc = M::lid();
-#pragma unroll
-    for (int t = 0; t < L; ++t) {
-        P[t] = acc;
-        if (s0 + t < n1) acc = M::lop(acc, M::lget(tile[t][tid]));
-    }
-    typename M::acc_t qv = Q ? M::get(Q[s * qs + c]) : M::id();
-    if (T) qv = M::op(qv, M::get(T[c]));
-    Lt sacc = M::lid();
-    SOut *dst = out + s0 * Mc + c;
-#pragma unroll
-    for (int t = L - 1; t >= 0; --t) {
-        if (s0 + k1 + t < n1) sacc = M::lop(M::lget(tile[tw + t][tid]), sacc);
-        if (s0 + t < n1) dst[t * Mc] = M::template put<SOut>(M::op(qv, M::widen(M::lop(P[t], sacc))));
     }
 }
 

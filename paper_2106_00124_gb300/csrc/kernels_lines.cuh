@@ -10,12 +10,9 @@
 //   k_inc_lines    BDBS-Along-Dim: the included sum of window k along each
 //                  line, by the k-blocked prefix and suffix scans and the
 //                  combine step of BDBS-1D (Sec. 3).
-//   k_reduce_seg   Reductions of fixed-length segments of each line (the
-//                  totals the dimension-reduction steps of Sec. 5 carry).
-//   k_sum_segs_*   Reduction of segment totals to column totals.
-//   k_carry_*      Per-segment carries of the prefix/suffix along dim 1.
-//   k_exline       Prefix-Along-Dim / Suffix-Along-Dim along dimension 1
-//                  fused with Add-Contribution (Sec. 5), per segment.
+//   k_carry_*      Per-segment carries of the prefix/suffix along dim 1
+//                  (the dimension-1 step itself is k_exline2 in
+//                  kernels_fast.cuh).
 #pragma once
 
 #include "monoid.cuh"
@@ -131,63 +128,6 @@ k_inc_lines(const SIn *__restrict__ in, SOut *__restrict__ out, int64_t O, int64
 }
 
 // ---------------------------------------------------------------------------
-// Segment reductions along dimension 1 of a view [n1, Mc] (row-major, Mc
-// columns).  Segment s covers rows [s*L, min(s*L+L, n1)).  R[s][c] is the
-// whole segment; Rt[s][c] (if non-null) the segment from offset r on.
-// ---------------------------------------------------------------------------
-template <class M, class SIn>
-__global__ void __launch_bounds__(256)
-k_reduce_seg(const SIn *__restrict__ X, typename M::car_t *__restrict__ R,
-             typename M::car_t *__restrict__ Rt, int64_t n1, int64_t Mc, int64_t L, int64_t S,
-             int64_t r)
-{
-    using A = typename M::acc_t;
-    using C = typename M::car_t;
-    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (gid >= S * Mc) return;
-    const int64_t c = gid % Mc, s = gid / Mc;
-    const int64_t y0 = s * L;
-    const int64_t y1 = (y0 + L < n1) ? y0 + L : n1;
-    const int64_t ys = (y0 + r < y1) ? y0 + r : y1;
-    A head = M::id(), tail = M::id();
-#pragma unroll 4
-    for (int64_t y = y0; y < ys; ++y) head = M::op(head, M::get(X[y * Mc + c]));
-#pragma unroll 4
-    for (int64_t y = ys; y < y1; ++y) tail = M::op(tail, M::get(X[y * Mc + c]));
-    R[gid] = M::template put<C>(M::op(head, tail));
-    if (Rt) Rt[gid] = M::template put<C>(tail);
-}
-
-// Column totals G[c] = (+)_s R[s][c]; one thread per column.
-template <class M>
-__global__ void __launch_bounds__(256)
-k_sum_segs_col(const typename M::car_t *__restrict__ R, typename M::car_t *__restrict__ G,
-               int64_t Mc, int64_t S)
-{
-    using A = typename M::acc_t;
-    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= Mc) return;
-    A acc = M::id();
-    for (int64_t s = 0; s < S; ++s) acc = M::op(acc, M::get(R[s * Mc + c]));
-    G[c] = M::template put<typename M::car_t>(acc);
-}
-
-// Column totals with one block per column (few columns, many segments).
-template <class M, int NT>
-__global__ void __launch_bounds__(NT)
-k_sum_segs_blk(const typename M::car_t *__restrict__ R, typename M::car_t *__restrict__ G,
-               int64_t Mc, int64_t S)
-{
-    using A = typename M::acc_t;
-    const int64_t c = blockIdx.x;
-    A acc = M::id();
-    for (int64_t s = threadIdx.x; s < S; s += NT) acc = M::op(acc, M::get(R[s * Mc + c]));
-    A pre, suf;
-    block_exscan_both<M, NT>(acc, pre, suf);
-    if (threadIdx.x == NT - 1) G[c] = M::template put<typename M::car_t>(M::op(pre, acc));
-}
-
-// ---------------------------------------------------------------------------
 // Carries of the dimension-1 prefix/suffix, per segment s and column c:
 //   Pc[s] = (+) of segments before s                       (exclusive prefix)
 //   W[s]  = (+) of rows >= (s+1)*L + k1                     (suffix past the
@@ -264,46 +204,6 @@ k_carry_blk(const typename M::car_t *__restrict__ R, const typename M::car_t *__
         }
         Q[s * Mc + c] = M::template put<C>(M::op(M::op(pc, w), tc));
         pc = M::op(pc, M::get(R[s * Mc + c]));
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Dimension-1 step of box-complement for one segment of one column
-// (view [n1, Mc]; segment s = rows [s*L, s*L+L)).  For x1 = s*L + t:
-//   out[x1][c] = Q (+) (+)_{u < t} H[s*L+u][c]              prefix, x1 excluded
-//                  (+) (+)_{v = t}^{L-1} H[s*L+k1+v][c]     suffix from x1+k1
-// Q carries the rest (segments before, rows past the target window, and the
-// lower-dimensional excluded sum).  This is Prefix-Along-Dim and
-// Suffix-Along-Dim along dimension 1 with the two Add-Contribution offsets
-// (-1 and +k1) of Fig. "exsum-code-full", evaluated per output instead of
-// per input.  The exclusive prefix is kept in L registers.
-// ---------------------------------------------------------------------------
-template <class M, class SIn, class SOut, int L>
-__global__ void __launch_bounds__(128)
-k_exline(const SIn *__restrict__ H, const typename M::car_t *__restrict__ Q, int64_t qs,
-         SOut *__restrict__ out, int64_t n1, int64_t Mc, int64_t k1, int64_t S)
-{
-    using A = typename M::acc_t;
-    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (gid >= S * Mc) return;
-    const int64_t c = gid % Mc, s = gid / Mc;
-    const int64_t s0 = s * L;
-    A P[L];
-    A acc = M::id();
-#pragma unroll
-    for (int t = 0; t < L; ++t) {
-        P[t] = acc;
-        const int64_t y = s0 + t;
-        if (y < n1) acc = M::op(acc, M::get(H[y * Mc + c]));
-    }
-    const A q = Q ? M::get(Q[s * qs + c]) : M::id();
-    A sacc = M::id();
-#pragma unroll
-    for (int t = L - 1; t >= 0; --t) {
-        const int64_t y = s0 + k1 + t;
-        if (y < n1) sacc = M::op(M::get(H[y * Mc + c]), sacc);
-        const int64_t x = s0 + t;
-        if (x < n1) out[x * Mc + c] = M::template put<SOut>(M::op(M::op(q, P[t]), sacc));
     }
 }
 

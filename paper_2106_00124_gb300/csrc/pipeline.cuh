@@ -25,7 +25,7 @@ enum { ST_OK = 0, ST_EINVAL = -1, ST_ENOMEM = -2, ST_EUNSUP = -3, ST_ECUDA = -4 
 enum KernelTag {
     TAG_INC = 0,          // BDBS-Along-Dim, generic line pass (k > 32)
     TAG_REDUCE = 1,       // segment / column reductions
-    TAG_SUMSEG = 2,       // segment totals -> column totals
+    TAG_SUMSEG = 2,       // (unused; kept so that tag numbers stay stable)
     TAG_CARRY = 3,        // dimension-1 carries
     TAG_EXLINE = 4,       // dimension-1 prefix/suffix + contributions
     TAG_INC_CONTIG = 5,   // BDBS-Along-Dim, contiguous dimension (k_inc_flat)
@@ -192,38 +192,6 @@ struct Pipe {
         cx.before(TAG_INC, O * n * I);
         kern<<<(unsigned)cdiv(total, threads), threads, smem, cx.stream>>>(src, dst, O, n, I, k, Lc,
                                                                            nchunks, gslots);
-        cx.check_launch();
-    }
-
-    // ---- column totals over dimension 1 of a view [n1, Mc] ----------------------------
-    template <class SIn>
-    static void colsum(Ctx &cx, const SIn *X, CAR *G, int64_t n1, int64_t Mc)
-    {
-        if (!cx.ok()) return;
-        int64_t S = cdiv(152 * 2048, Mc);
-        if (S > cdiv(n1, 8)) S = cdiv(n1, 8);
-        if (S < 1) S = 1;
-        const int64_t L = cdiv(n1, S);
-        S = cdiv(n1, L);
-        if (S == 1) {
-            if (cx.dry) return;
-            cx.before(TAG_REDUCE, n1 * Mc);
-            k_reduce_seg2<M, SIn><<<(unsigned)cdiv(Mc, 256), 256, 0, cx.stream>>>(X, G, nullptr, n1,
-                                                                                   Mc, L, 1, 0);
-            cx.check_launch();
-            return;
-        }
-        CAR *Rx = cx.take<CAR>(S * Mc);
-        if (cx.dry || !cx.ok()) return;
-        cx.before(TAG_REDUCE, n1 * Mc);
-        k_reduce_seg2<M, SIn><<<(unsigned)cdiv(S * Mc, 256), 256, 0, cx.stream>>>(X, Rx, nullptr, n1,
-                                                                                   Mc, L, S, 0);
-        cx.check_launch();
-        cx.before(TAG_SUMSEG, S * Mc);
-        if (Mc >= 1024)
-            k_sum_segs_col<M><<<(unsigned)cdiv(Mc, 256), 256, 0, cx.stream>>>(Rx, G, Mc, S);
-        else
-            k_sum_segs_blk<M, 256><<<(unsigned)Mc, 256, 0, cx.stream>>>(Rx, G, Mc, S);
         cx.check_launch();
     }
 
