@@ -102,6 +102,19 @@ size_t exsum_workspace_bytes(int d, const int64_t *shape, const int64_t *k, int 
 int exsum_included(const void *in, void *out, int d, const int64_t *shape, const int64_t *k,
                    int op, int dtype, void *stream);
 
+/*
+ * Weak excluded sums (BDBS complement; Sec. 1 and Sec. 6, "BDBSC"): the total
+ * of the tensor minus the included sum at each point.  This needs an inverse
+ * of the operator, so only integer + is supported (dtype EXSUM_I32 or
+ * EXSUM_I64; int32 and int64 + wrap modulo 2^32 and 2^64, which makes the
+ * result exact and equal to the strong excluded sum).  Other dtypes return
+ * EXSUM_EUNSUPPORTED.  Same arguments, ownership and workspace policy as
+ * exsum_included (op is +); `out` also holds the included sums during the
+ * call.  Runs on `stream` and returns without waiting.
+ */
+int exsum_excluded_weak(const void *in, void *out, int d, const int64_t *shape, const int64_t *k,
+                        int dtype, void *stream);
+
 /* As exsum_included, with a caller-owned DEVICE workspace of at least
  * exsum_workspace_bytes(..., excluded = 0) bytes (EXSUM_ENOMEM if smaller).
  * Allocates nothing; safe to capture in a CUDA graph. */

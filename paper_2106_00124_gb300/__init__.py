@@ -94,6 +94,8 @@ _SIG = {
                              ctypes.c_int, ctypes.c_int], ctypes.c_int),
     "exsum_kernel_name": ([ctypes.c_int], ctypes.c_char_p),
     "exsum_launch_count": ([], ctypes.c_int64),
+    "exsum_excluded_weak": ([_P, _P, ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
+                             ctypes.POINTER(ctypes.c_int64), ctypes.c_int, _P], ctypes.c_int),
     "exsum_graph_instantiate": ([_P, ctypes.POINTER(_P)], ctypes.c_int),
     "exsum_graph_launch": ([_P, _P], ctypes.c_int),
     "exsum_graph_exec_destroy": ([_P], ctypes.c_int),
@@ -186,6 +188,11 @@ def exsum_included(in_ptr, out_ptr, d, shape, k, op, dtype, stream=0):
 def exsum_excluded(in_ptr, out_ptr, d, shape, k, op, dtype, stream=0):
     return _load().exsum_excluded(in_ptr, out_ptr, int(d), _arr(shape), _arr(k), int(op),
                                   int(dtype), stream or None)
+
+
+def exsum_excluded_weak(in_ptr, out_ptr, d, shape, k, dtype, stream=0):
+    return _load().exsum_excluded_weak(in_ptr, out_ptr, int(d), _arr(shape), _arr(k), int(dtype),
+                                       stream or None)
 
 
 def exsum_included_ws(in_ptr, out_ptr, d, shape, k, op, dtype, ws_ptr, ws_bytes, stream=0):
@@ -372,3 +379,10 @@ def included(x, k, op="add", out=None):
 def excluded(x, k, op="add", out=None):
     """Strong excluded sums of a contiguous CUDA tensor (bf16 -> fp32 output)."""
     return _torch_call(exsum_excluded, x, k, op, out, "exsum_excluded")
+
+
+def excluded_weak(x, k, out=None):
+    """Weak excluded sums (total minus included) of a contiguous int32/int64
+    CUDA tensor, operator +."""
+    return _torch_call(lambda i, o, d, sh, kk, op, dt, st: exsum_excluded_weak(i, o, d, sh, kk, dt, st),
+                       x, k, "add", out, "exsum_excluded_weak")

@@ -248,6 +248,51 @@ static int call_cached(int excluded, const void *in, void *out, int d, const int
     return run(excluded, in, out, d, shape, k, op, dtype, ws, wsb, stream, nullptr);
 }
 
+// ---- weak excluded sums (total minus included; integer + only) ------------------------------
+namespace {
+// Total of the tensor modulo 2^64 (the low 32 bits are the int32 total
+// modulo 2^32): warp sums of a grid-stride walk, added atomically.
+template <class T>
+__global__ void __launch_bounds__(256) k_weak_total(const T *__restrict__ x, int64_t n,
+                                                     unsigned long long *__restrict__ acc)
+{
+    unsigned long long s = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        s += (unsigned long long)(long long)x[i];
+#pragma unroll
+    for (int m = 16; m > 0; m >>= 1) s += __shfl_xor_sync(0xffffffffu, s, m);
+    if ((threadIdx.x & 31) == 0) atomicAdd(acc, s);
+}
+
+// out[i] = total - out[i], wrapping.
+template <class T, class U>
+__global__ void __launch_bounds__(256) k_weak_finish(T *__restrict__ out, int64_t n,
+                                                      const unsigned long long *__restrict__ acc)
+{
+    const U tot = (U)*acc;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        out[i] = (T)(tot - (U)out[i]);
+}
+
+template <class T, class U>
+int weak_launch(const void *in, void *out, int64_t N, unsigned long long *acc, cudaStream_t st)
+{
+    int sms = 152, dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess)
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int64_t blocks = (N + 255) / 256;
+    if (blocks > (int64_t)sms * 8) blocks = (int64_t)sms * 8;
+    if (blocks < 1) blocks = 1;
+    exsum::trace_before(st, exsum::TAG_WEAK, 0, N);
+    k_weak_finish<T, U><<<(unsigned)blocks, 256, 0, st>>>((T *)out, N, acc);
+    exsum::trace_after(st);
+    (void)in;
+    return EXSUM_OK;
+}
+}  // namespace
+
 extern "C" {
 
 int exsum_version(void) { return 10000; }
@@ -293,6 +338,58 @@ size_t exsum_workspace_bytes(int d, const int64_t *shape, const int64_t *k, int 
     if (!rc) rc = run(excluded ? 1 : 0, nullptr, nullptr, d, shape, k, op, dtype, nullptr, 0, nullptr, &need);
     if (status) *status = rc;
     return rc ? 0 : need;
+}
+
+int exsum_excluded_weak(const void *in, void *out, int d, const int64_t *shape, const int64_t *k,
+                        int dtype, void *stream)
+{
+    int rc = validate(d, shape, k, EXSUM_OP_ADD, dtype);
+    if (rc) return rc;
+    if (dtype != EXSUM_I32 && dtype != EXSUM_I64) return EXSUM_EUNSUPPORTED;
+    if (!in || !out) return EXSUM_EINVAL;
+    int64_t N = 1;
+    for (int i = 0; i < d; ++i) N *= shape[i];
+    size_t need = 0;
+    rc = run(0, nullptr, nullptr, d, shape, k, EXSUM_OP_ADD, dtype, nullptr, 0, nullptr, &need);
+    if (rc) return rc;
+    const size_t inc_bytes = (need + 255) & ~(size_t)255;
+    void *ws = nullptr;
+    size_t wsb = 0;
+    rc = cached_workspace(stream, inc_bytes + 256, &ws, &wsb);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned long long *acc = (unsigned long long *)((char *)ws + inc_bytes);
+    cudaError_t ce = cudaMemsetAsync(acc, 0, sizeof(*acc), st);
+    if (ce == cudaSuccess) {
+        int sms = 152, dev = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess)
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        int64_t blocks = (N + 255) / 256;
+        if (blocks > (int64_t)sms * 8) blocks = (int64_t)sms * 8;
+        exsum::trace_before(st, exsum::TAG_REDUCE, 0, N);
+        if (dtype == EXSUM_I32)
+            k_weak_total<int32_t><<<(unsigned)blocks, 256, 0, st>>>((const int32_t *)in, N, acc);
+        else
+            k_weak_total<int64_t><<<(unsigned)blocks, 256, 0, st>>>((const int64_t *)in, N, acc);
+        exsum::trace_after(st);
+        ce = cudaGetLastError();
+    }
+    if (ce != cudaSuccess) {
+        g_last_cuda_error = (int)ce;
+        return EXSUM_ECUDA;
+    }
+    rc = run(0, in, out, d, shape, k, EXSUM_OP_ADD, dtype, ws, inc_bytes, stream, nullptr);
+    if (rc) return rc;
+    if (dtype == EXSUM_I32)
+        weak_launch<int32_t, uint32_t>(in, out, N, acc, st);
+    else
+        weak_launch<int64_t, uint64_t>(in, out, N, acc, st);
+    ce = cudaGetLastError();
+    if (ce != cudaSuccess) {
+        g_last_cuda_error = (int)ce;
+        return EXSUM_ECUDA;
+    }
+    return EXSUM_OK;
 }
 
 int exsum_included(const void *in, void *out, int d, const int64_t *shape, const int64_t *k, int op,
@@ -369,6 +466,7 @@ const char *exsum_kernel_name(int tag)
     case exsum::TAG_EXLINE: return "dim1_prefix_suffix_contrib";
     case exsum::TAG_ROWSUM: return "row_totals";
     case exsum::TAG_ROWX: return "row_prefix_suffix_contrib";
+    case exsum::TAG_WEAK: return "weak_total_minus_included";
     default: return "unknown";
     }
 }

@@ -32,7 +32,8 @@ enum KernelTag {
     TAG_INC_STRIDED = 6,  // BDBS-Along-Dim, strided dimension (k_inc_strided)
     TAG_ROWSUM = 7,       // row totals over the last dimension (k_row_totals)
     TAG_ROWX = 8,         // last-dimension prefix/suffix + contributions (k_rowx)
-    TAG_COUNT = 9
+    TAG_WEAK = 9,         // weak excluded sums: total, then total minus included
+    TAG_COUNT = 10
 };
 
 // Launch bracketing for the trace and the launch counter (exsum_abi.cu).
