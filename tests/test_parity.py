@@ -91,3 +91,30 @@ def test_repeat_calls_identical():
     a = gpu_sum("excluded", x, (4, 8, 16), "add")
     b = gpu_sum("excluded", x, (4, 8, 16), "add")
     assert np.array_equal(a, b)
+
+
+# Inputs and outputs one element past an aligned allocation: the staged,
+# vectorised and 16-byte-store paths must fall back to element accesses.
+MISALIGNED = [((9, 17, 33), (2, 8, 5)), ((3, 100, 256), (2, 9, 17)), ((29, 3, 20), (3, 2, 5)),
+              ((64, 64), (16, 16)), ((40, 5, 72), (3, 1, 8)), ((300, 3), (7, 2))]
+
+
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("shape,k", MISALIGNED, ids=[str(c[0]) + "k" + str(c[1]) for c in MISALIGNED])
+def test_parity_misaligned(shape, k, dtype, kind):
+    import torch
+    import paper_2106_00124_gb300 as ex
+    dev, vals = seeded(shape, dtype, 991, "add")
+    x0 = to_device(dev, dtype)
+    n = x0.numel()
+    x = torch.empty(n + 1, dtype=x0.dtype, device="cuda")[1:].view(shape)
+    x.copy_(x0)
+    out_dt = torch.float32 if dtype == "bf16" else x0.dtype
+    out = torch.empty(n + 1, dtype=out_dt, device="cuda")[1:].view(shape)
+    assert x.data_ptr() % 16 != 0 and out.data_ptr() % 16 != 0
+    fn = ex.excluded if kind == "excluded" else ex.included
+    fn(x, k, "add", out=out)
+    torch.cuda.synchronize()
+    check(out.cpu().numpy(), oracle_sum(kind, vals, k, "add"), dtype, "add",
+          "misaligned %s %s %s k=%s" % (kind, dtype, shape, k))
