@@ -18,7 +18,7 @@ on the stream it runs on, and between steps a
 capture of the same step with the library's launch trace on (event-record
 nodes around every kernel node), replayed K more times inside the timed
 region and read back after each replay.  `e2e` calls the C ABI directly
-(no graph) with pinned host input and output buffers, two lanes in flight.
+(no graph) with pinned host input and output buffers, three lanes in flight.
 """
 
 import argparse
@@ -344,12 +344,13 @@ def run_ours(args):
     # ---- end to end through the public API with host buffers ----------------------------------
     # Every step copies its input from pinned host memory, runs the excluded
     # sum through the C ABI and copies the result back to pinned host memory.
-    # Consecutive steps alternate between two lanes (stream + device buffers +
-    # workspace each), so one step's copies overlap the next step's work, as a
-    # caller streaming independent tensors would run them.
+    # Consecutive steps rotate over three lanes (stream + device buffers +
+    # workspace each), so one step's copies overlap the other steps' copies
+    # and work, as a caller streaming independent tensors would run them.
+    # The host link bounds this (both copy directions at once share it).
     e2e = None
     if not args.no_e2e:
-        lanes = 2
+        lanes = 3
         host_in = torch.empty(x.shape, dtype=x.dtype, pin_memory=True)
         host_in.copy_(x.cpu())
         lane = []
