@@ -292,6 +292,18 @@ int64_t exsum_server_completed(exsum_server *srv);
 void exsum_server_destroy(exsum_server *srv);
 
 /*
+ * Host-side fault injection for tests of the failure path (no counterpart in
+ * the paper).  The next `count` requests the server admits are not launched:
+ * each ends as if its launch had returned `status` (a negative EXSUM_E*
+ * code), releases its memory and slot through the same stream-ordered
+ * completion as a real failure, and exsum_server_wait returns `status` for
+ * it.  count = 0 switches injection off.  Nothing reaches the GPU, so no
+ * device fault is involved.  Returns EXSUM_EINVAL for a NULL server, a
+ * negative count or a non-negative status.
+ */
+int exsum_server_fail_next(exsum_server *srv, int count, int status);
+
+/*
  * Launch trace.  The paper reports time per element (Sec. 6); this breaks a
  * call's device time down by pass.  While enabled, every kernel the library
  * launches is bracketed by a pair of CUDA events recorded on the stream it

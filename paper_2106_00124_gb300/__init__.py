@@ -118,6 +118,7 @@ _SIG = {
                                   ctypes.c_int),
     "exsum_server_release": ([_P, ctypes.c_uint64], ctypes.c_int),
     "exsum_server_completed": ([_P], ctypes.c_int64),
+    "exsum_server_fail_next": ([_P, ctypes.c_int, ctypes.c_int], ctypes.c_int),
     "exsum_server_destroy": ([_P], None),
 }
 
@@ -333,6 +334,11 @@ def exsum_server_release(server, ticket):
 
 def exsum_server_completed(server):
     return int(_load().exsum_server_completed(server))
+
+
+def exsum_server_fail_next(server, count, status):
+    """Host-side fault injection: the next `count` admitted requests end with `status`."""
+    return _load().exsum_server_fail_next(server, int(count), int(status))
 
 
 def exsum_server_destroy(server):

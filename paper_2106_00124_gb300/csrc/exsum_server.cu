@@ -117,13 +117,19 @@ struct exsum_server {
     bool stop = false;
     std::thread worker;
     int64_t completed = 0;
+    int fail_next = 0;               // host-side fault injection (exsum_server_fail_next)
+    int fail_status = EXSUM_OK;
 };
 
 namespace {
 
+// What the stream-ordered callback needs: the request, and the status it
+// ends with (a failed launch passes its error here, so that `done` and
+// `status` change together under the lock).
 struct Completion {
     exsum_server *srv;
     uint64_t ticket;
+    int status;
 };
 
 void CUDART_CB on_complete(void *data)
@@ -137,6 +143,7 @@ void CUDART_CB on_complete(void *data)
             Request &r = it->second;
             srv->arena.release(r.off, r.need);
             srv->slot_busy[r.slot] = 0;
+            if (c->status != EXSUM_OK) r.status = c->status;
             r.done = true;
             r.t_done = now_ns();
             srv->completed++;
@@ -170,7 +177,7 @@ int launch(exsum_server *srv, Request &r)
         if (cudaMemcpyAsync(r.desc.out, out, r.out_bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess)
             return EXSUM_ECUDA;
     }
-    Completion *c = new Completion{srv, r.ticket};
+    Completion *c = new Completion{srv, r.ticket, EXSUM_OK};
     if (cudaLaunchHostFunc(s, on_complete, c) != cudaSuccess) {
         delete c;
         return EXSUM_ECUDA;
@@ -209,15 +216,20 @@ void worker_main(exsum_server *srv)
             head.t_start = now_ns();
             srv->slot_busy[slot] = 1;
             Request r = head;   // a copy: the map may change while unlocked
+            int inject = EXSUM_OK;
+            if (srv->fail_next > 0) {
+                srv->fail_next--;
+                inject = srv->fail_status;
+            }
             lock.unlock();
-            const int rc = launch(srv, r);
+            const int rc = inject != EXSUM_OK ? inject : launch(srv, r);
             int rc2 = EXSUM_OK;
             if (rc) {
                 // Whatever was queued before the failure may still run: let
                 // the stream release the request's memory and slot once it
                 // drains.
                 cudaGetLastError();
-                Completion *c = new Completion{srv, r.ticket};
+                Completion *c = new Completion{srv, r.ticket, rc};
                 if (cudaLaunchHostFunc(srv->slots[slot], on_complete, c) != cudaSuccess) {
                     delete c;
                     cudaGetLastError();
@@ -225,16 +237,22 @@ void worker_main(exsum_server *srv)
                 }
             }
             lock.lock();
-            if (rc) {
-                Request &q = srv->reqs[r.ticket];
-                q.status = rc;
-                if (rc2) {
-                    // the request's arena block stays reserved until the server is destroyed
-                    srv->slot_busy[slot] = 0;
-                    q.done = true;
-                    q.t_done = now_ns();
-                    srv->cv_done.notify_all();
+            if (rc && rc2) {
+                // No callback could be queued, so none will complete the
+                // request: do it here.  Its arena block stays reserved until
+                // the server is destroyed (work queued before the failure
+                // may still use it).  When the callback was queued, it sets
+                // the status together with `done`; the request may even be
+                // released already, so it is not looked up here.
+                auto it = srv->reqs.find(r.ticket);
+                if (it != srv->reqs.end()) {
+                    it->second.status = rc;
+                    it->second.done = true;
+                    it->second.t_done = now_ns();
+                    srv->completed++;
                 }
+                srv->slot_busy[slot] = 0;
+                srv->cv_done.notify_all();
             }
         }
         if (srv->stop && srv->pending.empty()) break;
@@ -337,12 +355,18 @@ int exsum_server_wait(exsum_server *srv, uint64_t ticket, int64_t timeout_ns)
     if (it == srv->reqs.end()) return EXSUM_EINVAL;
     const auto deadline = std::chrono::steady_clock::now() +
                           std::chrono::nanoseconds(timeout_ns < 0 ? 0 : timeout_ns);
-    while (!srv->reqs[ticket].done) {
-        if (srv->cv_done.wait_until(lock, deadline) == std::cv_status::timeout &&
-            !srv->reqs[ticket].done)
-            return EXSUM_ETIMEDOUT;
+    // Looked up again after every wake: another thread may release the
+    // ticket while this one waits.
+    while (true) {
+        it = srv->reqs.find(ticket);
+        if (it == srv->reqs.end()) return EXSUM_EINVAL;
+        if (it->second.done) return it->second.status;
+        if (srv->cv_done.wait_until(lock, deadline) == std::cv_status::timeout) {
+            it = srv->reqs.find(ticket);
+            if (it == srv->reqs.end()) return EXSUM_EINVAL;
+            return it->second.done ? it->second.status : EXSUM_ETIMEDOUT;
+        }
     }
-    return srv->reqs[ticket].status;
 }
 
 int exsum_server_ticket_times(exsum_server *srv, uint64_t ticket, int64_t *submit_ns,
@@ -371,6 +395,15 @@ int exsum_server_release(exsum_server *srv, uint64_t ticket)
 }
 
 int64_t exsum_server_now_ns(void) { return now_ns(); }
+
+int exsum_server_fail_next(exsum_server *srv, int count, int status)
+{
+    if (!srv || count < 0 || status >= 0) return EXSUM_EINVAL;
+    std::lock_guard<std::mutex> lock(srv->mu);
+    srv->fail_next = count;
+    srv->fail_status = status;
+    return EXSUM_OK;
+}
 
 int64_t exsum_server_completed(exsum_server *srv)
 {

@@ -9,11 +9,13 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <type_traits>
 
 #include "kernels_flat.cuh"
+#include "kernels_rowbulk.cuh"
 #include "kernels_rows.cuh"
 
 namespace exsum {
@@ -57,6 +59,7 @@ struct Ctx {
     int status = ST_OK;
     cudaError_t cuda_err = cudaSuccess;
     int level = 0;           // recursion depth of box-complement (0 = input tensor)
+    int64_t sms = 152;       // streaming multiprocessors of the device
 
     template <class T>
     T *take(int64_t count)
@@ -82,6 +85,28 @@ struct Ctx {
 };
 
 static inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Streaming multiprocessors of the current device, looked up once per device
+// (grids and tile heights are sized by it).  Without a usable device (a
+// workspace query on a machine with no GPU) the GB300's 152 is assumed.
+inline int device_sms()
+{
+    static int cache[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return 152;
+    }
+    if (cache[dev] <= 0) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) {
+            cudaGetLastError();
+            v = 152;
+        }
+        cache[dev] = v;
+    }
+    return cache[dev];
+}
 
 template <class M>
 struct Pipe {
@@ -134,7 +159,7 @@ struct Pipe {
                     // Four inner positions per thread, 16-byte accesses;
                     // chunks short enough for ~1024 threads per SM.
                     int Lc = 128;
-                    while (Lc > 2 * k && Lc > 16 && O * cdiv(n, Lc) * (I / 4) < 152 * 1024) Lc >>= 1;
+                    while (Lc > 2 * k && Lc > 16 && O * cdiv(n, Lc) * (I / 4) < cx.sms * 1024) Lc >>= 1;
                     if (Lc > n) Lc = (int)n;
                     const int nchunks = (int)cdiv(n, Lc);
                     const int64_t total = O * nchunks * (I / 4);
@@ -147,7 +172,7 @@ struct Pipe {
             }
             // Chunks short enough for ~2048 threads per SM (walks of a few blocks).
             int Lc = 128;
-            while (Lc > 2 * k && Lc > 16 && O * cdiv(n, Lc) * I < 152 * 2048) Lc >>= 1;
+            while (Lc > 2 * k && Lc > 16 && O * cdiv(n, Lc) * I < cx.sms * 2048) Lc >>= 1;
             if (Lc > n) Lc = (int)n;
             const int nchunks = (int)cdiv(n, Lc);
             const int64_t total = O * nchunks * I;
@@ -316,7 +341,7 @@ struct Pipe {
     // window along n_{d-1} is fused when the staged halo (k2 - 1 rows) is at
     // most about half the tile, or the tile is the whole slice; small tensors
     // get shorter tiles (more blocks) down to that limit.
-    static RowPlan row_plan(int d, const int64_t *n, const int64_t *k)
+    static RowPlan row_plan(int d, const int64_t *n, const int64_t *k, int64_t sms)
     {
         RowPlan rp;
         if (d < 2) return rp;
@@ -340,7 +365,7 @@ struct Pipe {
         if (GO > O2) GO = O2;
         const int64_t groups = cdiv(O2, GO);
         // rows per tile for at least two blocks per SM, when the tensor has them
-        const int64_t tr_par = groups >= 2 * 152 ? n2 : cdiv(n2, cdiv(2 * 152, groups));
+        const int64_t tr_par = groups >= 2 * sms ? n2 : cdiv(n2, cdiv(2 * sms, groups));
         // rows a tile holds: TR, the k2 - 1 halo rows and the identity rows the
         // column walk may read past them
         auto rows_held = [&](int64_t tr, bool f) -> int64_t {
@@ -415,6 +440,143 @@ struct Pipe {
             cx.status = ST_EUNSUP;  // not reachable: row_plan gives one of the widths above
     }
 
+    // ---- final pass staged by bulk copies (kernels_rowbulk.cuh) ---------------------------
+    struct BulkPlan {
+        bool ok = false, aligned = false;
+        int TR = 0, epl = 32, lpr = 8, LSW = 0, nbuf = 2, nt = 256;
+        size_t smem = 0;
+        int ntiles = 0, grid = 0, ntile = 0;
+    };
+
+    static int env_int(const char *name, int dflt)
+    {
+        const char *v = getenv(name);
+        return (v && *v) ? atoi(v) : dflt;
+    }
+
+    // Geometry of k_rowx_bulk for rows of L elements, a window of kk rows
+    // along n2 (1: none; kmax its compile-time bound) and O2 slices of n2
+    // rows.  Strips of 32 elements (16 for L <= 128); NT = 256 threads with
+    // two staging buffers; the tallest tile (at most 64 rows, a multiple of
+    // the rows one row pass covers and of the walk's segments) that lets
+    // two blocks share an SM, else one.  EXSUM_ROWX_TR, EXSUM_ROWX_NBUF,
+    // EXSUM_ROWX_EPL and EXSUM_ROWX_NT override (tuning).
+    static BulkPlan bulk_plan(int64_t L, int64_t n2, int64_t O2, int kk, int kmax, int64_t sms)
+    {
+        BulkPlan bp;
+        if (sizeof(L_) != 4 || (L & 3) || L < 128 || L > 1024 || kk > 32) return bp;
+        int epl = env_int("EXSUM_ROWX_EPL", 0);
+        if (epl != 16 && epl != 32) epl = L <= 128 ? 16 : 32;
+        int lpr = 32;
+        while (lpr > 4 && (int64_t)(lpr / 2) * epl >= L) lpr >>= 1;
+        if ((int64_t)lpr * epl < L) return bp;
+        const int LP = lpr * epl;
+        const int LSW = (LP + 31) & ~31;
+        const int nt = env_int("EXSUM_ROWX_NT", 256) == 512 ? 512 : 256;
+        const int nbuf = env_int("EXSUM_ROWX_NBUF", 2) == 1 ? 1 : 2;
+        const int rows_pass = (nt / 32) * (32 / lpr);
+        const int G = rowbulk_segs((int)L, kmax, nt);
+        int step = rows_pass;
+        while (step % G) step += rows_pass;
+        const bool kfull = kk > 1 && kk == kmax;
+        if (kfull)
+            while ((step / G) % kk) step += rows_pass;
+        const int tr_env = env_int("EXSUM_ROWX_TR", 0);
+        auto sm = [&](int tr) {
+            const bool al = kfull && (tr / G) % kk == 0 && tr % G == 0;
+            return rowbulk_smem(tr, kk, al, (int)L, LSW, nbuf);
+        };
+        const size_t two = 113 * 1024, one = 226 * 1024;
+        int TR = 0, bps = nt == 512 ? 1 : 2;
+        if (tr_env > 0) {
+            TR = (tr_env + step - 1) / step * step;
+            if (sm(TR) > two) bps = 1;
+        } else {
+            const size_t lim = bps == 2 ? two : one;
+            for (int tr = (64 / step) * step; tr >= step && !TR; tr -= step)
+                if (sm(tr) <= lim) TR = tr;
+            if (!TR && bps == 2) {
+                bps = 1;
+                for (int tr = (64 / step) * step; tr >= step && !TR; tr -= step)
+                    if (sm(tr) <= one) TR = tr;
+            }
+        }
+        if (!TR) return bp;
+        const size_t smem = sm(TR);
+        if (smem > one) return bp;
+        const int64_t ntile = cdiv(n2, TR);
+        if (O2 * ntile >= (1ll << 31)) return bp;
+        bp.ok = true;
+        bp.aligned = kfull && (TR / G) % kk == 0 && TR % G == 0;
+        bp.TR = TR;
+        bp.epl = epl;
+        bp.lpr = lpr;
+        bp.LSW = LSW;
+        bp.nbuf = nbuf;
+        bp.nt = nt;
+        bp.smem = smem;
+        bp.ntile = (int)ntile;
+        bp.ntiles = (int)(O2 * ntile);
+        bp.grid = (int)(bp.ntiles < sms * bps ? bp.ntiles : sms * bps);
+        return bp;
+    }
+
+    template <class SOut, int KM, int EPL, int NB, int NT>
+    static void rowbulk_go(Ctx &cx, const BulkPlan &bp, const L_ *src, const CAR *T, SOut *out,
+                           int64_t n2, int64_t L, int kk, int k3)
+    {
+        auto kern = k_rowx_bulk<M, SOut, KM, EPL, NB, NT>;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bp.smem);
+        kern<<<(unsigned)bp.grid, NT, bp.smem, cx.stream>>>(src, T, out, bp.ntiles, bp.ntile, (int)n2,
+                                                            (int)L, kk, k3, bp.TR, bp.LSW, bp.lpr,
+                                                            bp.aligned ? 1 : 0);
+    }
+
+    template <class SOut, int KM>
+    static void rowbulk_epl(Ctx &cx, const BulkPlan &bp, const L_ *src, const CAR *T, SOut *out,
+                            int64_t n2, int64_t L, int kk, int k3)
+    {
+        if (bp.nt == 512)
+            rowbulk_go<SOut, KM, 32, 2, 512>(cx, bp, src, T, out, n2, L, kk, k3);
+        else if (bp.nbuf == 1)
+            rowbulk_go<SOut, KM, 32, 1, 256>(cx, bp, src, T, out, n2, L, kk, k3);
+        else if (bp.epl == 16)
+            rowbulk_go<SOut, KM, 16, 2, 256>(cx, bp, src, T, out, n2, L, kk, k3);
+        else
+            rowbulk_go<SOut, KM, 32, 2, 256>(cx, bp, src, T, out, n2, L, kk, k3);
+    }
+
+    // Launches k_rowx_bulk when the pass qualifies (4-byte local type read
+    // as is, 16-byte aligned input and output, 128 <= L <= 1024, L % 4 == 0,
+    // no one-dimensional tail); returns false otherwise.
+    template <class SF, class SOut>
+    static bool rowbulk_try(Ctx &cx, const SF *src, const CAR *T, SOut *out, int64_t O2, int64_t n2,
+                            int64_t L, int kk, int k3)
+    {
+        if constexpr (sizeof(L_) == 4 && std::is_same<SF, L_>::value && sizeof(SOut) == 4) {
+            if (env_int("EXSUM_ROWX_KERNEL", 1) == 0) return false;
+            if ((((uintptr_t)src) & 15) || (((uintptr_t)out) & 15)) return false;
+            const int kmax = kk <= 1 ? 1 : kk <= 4 ? 4 : kk <= 8 ? 8 : kk <= 16 ? 16 : 32;
+            BulkPlan bp = bulk_plan(L, n2, O2, kk, kmax, cx.sms);
+            if (!bp.ok) return false;
+            if (bp.nt == 512 && bp.epl != 32) return false;
+            if (bp.nbuf == 1 && bp.epl != 32) return false;
+            if (kmax == 1)
+                rowbulk_epl<SOut, 1>(cx, bp, src, T, out, n2, L, 1, k3);
+            else if (kmax == 4)
+                rowbulk_epl<SOut, 4>(cx, bp, src, T, out, n2, L, kk, k3);
+            else if (kmax == 8)
+                rowbulk_epl<SOut, 8>(cx, bp, src, T, out, n2, L, kk, k3);
+            else if (kmax == 16)
+                rowbulk_epl<SOut, 16>(cx, bp, src, T, out, n2, L, kk, k3);
+            else
+                rowbulk_epl<SOut, 32>(cx, bp, src, T, out, n2, L, kk, k3);
+            return true;
+        } else {
+            return false;
+        }
+    }
+
     template <class SF, class SOut>
     static void rowx_launch(Ctx &cx, const RowPlan &rp, const SF *src, const CAR *T, const CAR *R1, SOut *out,
                             int64_t O2, int64_t n2, int64_t L, int64_t k2, int64_t k3)
@@ -424,6 +586,10 @@ struct Pipe {
         const int k1 = R1 ? (int)k2 : 0;
         cx.before(TAG_ROWX, O2 * n2 * L);
         const int kk = rp.fuse ? (int)k2 : 1;
+        if (!R1 && rowbulk_try<SF, SOut>(cx, src, T, out, O2, n2, L, kk, (int)k3)) {
+            cx.check_launch();
+            return;
+        }
         if (!rp.fuse)
             rowx_go<SF, SOut, 1>(cx, rp, src, T, R1, out, O2, n2, L, 1, (int)k3, k1);
         else if (kk <= 4)
@@ -474,7 +640,7 @@ struct Pipe {
             cx.before(TAG_ROWSUM, N);
             const int lpr = row_lanes(L);
             int64_t blocks = cdiv(rows, 8 * 4 * (32 / lpr));
-            if (blocks > 152 * 8) blocks = 152 * 8;
+            if (blocks > cx.sms * 8) blocks = cx.sms * 8;
             if (lpr <= 4)
                 k_row_totals<M, SIn, 4><<<(unsigned)blocks, 256, 0, cx.stream>>>(X, R, rows, (int)L);
             else if (lpr == 8)
@@ -538,7 +704,7 @@ struct Pipe {
             exline_stage<SIn, SOut>(cx, X, nullptr, out, n[0], 1, k[0]);
             return;
         }
-        const RowPlan rp = row_plan(d, n, k);
+        const RowPlan rp = row_plan(d, n, k, cx.sms);
         if (rp.ok) {
             excluded_rows<SIn, SOut>(cx, rp, X, out, d, n, k);
             return;
@@ -674,6 +840,7 @@ struct Pipe {
     {
         Ctx cx;
         cx.dry = true;
+        cx.sms = device_sms();
         if (excluded_sum)
             excluded<IN, OUT>(cx, nullptr, nullptr, d, n, k);
         else
@@ -684,6 +851,7 @@ struct Pipe {
         if (need > ws_bytes || (need > 0 && !ws)) return ST_ENOMEM;
         Ctx rx;
         rx.dry = false;
+        rx.sms = cx.sms;
         rx.base = (char *)ws;
         rx.cap = ws_bytes;
         rx.stream = stream;

@@ -54,13 +54,14 @@ def test_full_size_workload(name, kind):
 
 def test_server_stress_scheduled_arrivals():
     """400 mixed requests with scheduled arrivals on 4 slots and a budget that
-    holds only a few at a time: all complete, each equal to its lone result."""
+    holds only a few at a time: all complete, each equal to its lone result,
+    and the result of every distinct shape equal to the oracle's."""
     import torch
     import paper_2106_00124_gb300 as ex
     shapes = synth.batched_shapes(12, seed=21, side_lo=16, side_hi=96)
-    xs = [to_device(synth.make_input(s_, "f32", 30 + i)[0], "f32") for i, (s_, _) in
-          enumerate(shapes)]
-    outs = [torch.empty_like(x) for x in xs]
+    inputs = [synth.make_input(s_, "f32", 30 + i) for i, (s_, _) in enumerate(shapes)]
+    xs = [to_device(dev, "f32") for dev, _ in inputs]
+    outs = [torch.full_like(x, float("nan")) for x in xs]
     alone = []
     for x, (s_, k) in zip(xs, shapes):
         r = ex.excluded(x, k, "add")
@@ -73,9 +74,11 @@ def test_server_stress_scheduled_arrivals():
     t0 = ex.exsum_server_now_ns() + 20_000_000
     arrivals = t0 + np.cumsum(rng.exponential(20_000, size=400)).astype(np.int64)
     tickets = []
+    served = set()
     try:
         for i in range(400):
-            j = int(rng.integers(0, len(shapes)))
+            j = i if i < len(shapes) else int(rng.integers(0, len(shapes)))
+            served.add(j)
             s_, k = shapes[j]
             dsc = ex.make_desc(xs[j].data_ptr(), outs[j].data_ptr(), s_, k, ex.OP_ADD, ex.F32)
             rc, t = ex.exsum_server_submit_at(srv, dsc, 0, int(arrivals[i]))
@@ -89,5 +92,9 @@ def test_server_stress_scheduled_arrivals():
     finally:
         ex.exsum_server_destroy(srv)
     torch.cuda.synchronize()
-    for o, a in zip(outs, alone):
-        assert torch.equal(o, a)
+    for j in served:
+        assert torch.equal(outs[j], alone[j])
+        s_, k = shapes[j]
+        check(outs[j].cpu().numpy(), oracle_sum("excluded", inputs[j][1], k, "add"), "f32", "add",
+              "served shape %d" % j)
+    assert len(served) == len(shapes)
