@@ -467,6 +467,9 @@ const char *exsum_kernel_name(int tag)
     case exsum::TAG_ROWSUM: return "row_totals";
     case exsum::TAG_ROWX: return "row_prefix_suffix_contrib";
     case exsum::TAG_WEAK: return "weak_total_minus_included";
+    case exsum::TAG_INC_FOLD: return "bdbs_along_dim_strided_row_totals";
+    case exsum::TAG_PLANE: return "plane_totals";
+    case exsum::TAG_EXC2D: return "excluded_2d_lower";
     default: return "unknown";
     }
 }

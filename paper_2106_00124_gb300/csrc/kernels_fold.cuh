@@ -1,0 +1,259 @@
+// kernels_fold.cuh -- the row totals folded into the first strided pass, and
+// the two-dimensional lower problem of the row schedule in two short kernels.
+//
+// For d = 3 the row schedule needs R[x1, x2] = (+)_{x3} X[x1, x2, x3] (the
+// dimension reduction along the last dimension, Sec. 4) and the excluded
+// sum T of R with box (k1, k2).  Reading X once more just for R costs a
+// third of the tensor's traffic.  Instead the strided BDBS pass along
+// dimension 1, which reads all of X anyway, also leaves partial row totals
+// (one per 128 consecutive elements of a row), and
+//   k_plane_totals  combines them into R and the plane totals
+//                   R2[x1] = (+)_{x2} R[x1, x2],
+//   k_exc2d         forms T[x1, x2] = T2[x1] (+) (+)_{y2 < x2} H1[x1, y2]
+//                                     (+) (+)_{y2 >= x2 + k2} H1[x1, y2]
+//                   with T2 the one-dimensional excluded sum of R2 (box k1)
+//                   and H1 the window of k1 planes of R -- the row schedule
+//                   once more, one block per x1 (Sec. 4, Theorem "Recursive
+//                   Box-complement", the last dimension peeled).
+// Every reduction runs in a fixed order, so results do not depend on timing.
+#pragma once
+
+#include "kernels_flat.cuh"
+
+namespace exsum {
+
+// ---------------------------------------------------------------------------
+// BDBS-Along-Dim along dimension 1 (view [n, I], I % 128 == 0, 16-byte
+// aligned rows, 4-byte local type) as k_inc_strided4, with row totals: the
+// 32 lanes of a warp hold 128 consecutive inner positions, which lie in one
+// row of length L (L % 128 == 0).  Every input row of the thread's chunk
+// (Lc <= 32 rows) is reduced over its 4 columns as it is loaded, the 32
+// lanes' values go to shared memory, and lane l adds up row r0 + l in lane
+// order: Rp[(x1 * (I / L) + row) * H + h] = (+) of the 128 inputs, H = L / 128.
+// ---------------------------------------------------------------------------
+template <class M, class SIn, class SOut, int KMAX>
+__global__ void __launch_bounds__(128)
+k_inc_strided4_rt(const SIn *__restrict__ in, SOut *__restrict__ out, int n, int64_t I, int k, int Lc,
+                  int nchunks, int L, typename M::loc_t *__restrict__ Rp)
+{
+    using Lt = typename M::loc_t;
+    static_assert(sizeof(Lt) == 4, "4-byte local type");
+    __shared__ Lt rp[4][32][33];
+    const int64_t I4 = I >> 2;
+    const int64_t total = nchunks * I4;
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= total) return;   // whole warps: total is a multiple of 32
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t i4 = gid % I4;
+    const int ch = (int)(gid / I4);
+    const SIn *src = in + 4 * i4;
+    SOut *dst = out + 4 * i4;
+    const int r0 = ch * Lc;
+    const int rend = min(r0 + Lc, n);
+    const uint64_t pol_in = l2_policy_evict_first();
+    const uint64_t pol_out = l2_policy_evict_last();
+    Lt(*acc)[33] = rp[warp];
+    auto note = [&](int x, const Lt *v) {
+        if (x < rend) acc[x - r0][lane] = M::lop(M::lop(v[0], v[1]), M::lop(v[2], v[3]));
+    };
+    // (row totals are noted after all loads of a block are issued: a shared
+    // store between the loads would hold each load back until the previous
+    // one returns)
+    Lt S[KMAX][4], v[KMAX][4];
+#pragma unroll
+    for (int j = 0; j < KMAX; ++j) {
+        if (j < k && r0 + j < n) {
+            load4<M>(src + (int64_t)(r0 + j) * I, true, 4, v[j], pol_in);
+        } else {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) v[j][c] = M::lid();
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < KMAX; ++j)
+        if (j < k) note(r0 + j, v[j]);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) S[KMAX - 1][c] = v[KMAX - 1][c];
+#pragma unroll
+    for (int j = KMAX - 2; j >= 0; --j)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) S[j][c] = M::lop(v[j][c], S[j + 1][c]);
+    for (int sb = r0; sb < rend; sb += k) {
+        store4<M>(dst + (int64_t)sb * I, true, 4, S[0], pol_out);
+        const int nb = sb + k;
+#pragma unroll
+        for (int j = 0; j < KMAX; ++j) {
+            if (j < k && nb + j < n) {
+                load4<M>(src + (int64_t)(nb + j) * I, true, 4, v[j], pol_in);
+            } else {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) v[j][c] = M::lid();
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < KMAX; ++j)
+            if (j < k) note(nb + j, v[j]);
+        Lt p[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) p[c] = v[0][c];
+#pragma unroll
+        for (int j = 0; j + 1 < KMAX; ++j) {
+            Lt w[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                if (j > 0) p[c] = M::lop(p[c], v[j][c]);
+                w[c] = M::lop(S[j + 1][c], p[c]);
+            }
+            if (j + 1 < k && sb + 1 + j < rend) store4<M>(dst + (int64_t)(sb + 1 + j) * I, true, 4, w, pol_out);
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) S[KMAX - 1][c] = v[KMAX - 1][c];
+#pragma unroll
+        for (int j = KMAX - 2; j >= 0; --j)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) S[j][c] = M::lop(v[j][c], S[j + 1][c]);
+    }
+    __syncwarp();
+    const int x = r0 + lane;
+    if (x < rend) {
+        Lt t = acc[lane][0];
+#pragma unroll
+        for (int c = 1; c < 32; ++c) t = M::lop(t, acc[lane][c]);
+        const int64_t p0 = 4 * (i4 - lane);   // first inner position of the warp
+        const int64_t rows_per_x1 = I / L;
+        const int H = L >> 7;
+        Rp[((int64_t)x * rows_per_x1 + p0 / L) * H + (int)((p0 % L) >> 7)] = t;
+    }
+}
+
+// Block-wide combine of one value per thread, in a fixed order (butterfly
+// within warps, then warp 0 over the warp results); the result is returned
+// to every thread.  `red` holds at least blockDim.x / 32 values.
+template <class M>
+__device__ __forceinline__ typename M::acc_t block_reduce(typename M::acc_t v, typename M::acc_t *red)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int m = 16; m > 0; m >>= 1) v = M::op(v, shfl_xor(v, m));
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        v = lane < nw ? red[lane] : M::id();
+#pragma unroll
+        for (int m = 16; m > 0; m >>= 1) v = M::op(v, shfl_xor(v, m));
+        if (lane == 0) red[32] = v;
+    }
+    __syncthreads();
+    return red[32];
+}
+
+// ---------------------------------------------------------------------------
+// Plane totals: block x1 combines the H partial row totals of each row x2
+// (R[x1, x2], written unless R is null) and their total over x2 (R2[x1]).
+// ---------------------------------------------------------------------------
+template <class M, class SP>
+__global__ void __launch_bounds__(256)
+k_plane_totals(const SP *__restrict__ P, int H, typename M::car_t *__restrict__ R,
+               typename M::car_t *__restrict__ R2, int n2)
+{
+    using A = typename M::acc_t;
+    using C = typename M::car_t;
+    __shared__ A red[33];
+    const int64_t x1 = blockIdx.x;
+    A tot = M::id();
+    for (int x2 = threadIdx.x; x2 < n2; x2 += blockDim.x) {
+        const SP *p = P + (x1 * n2 + x2) * H;
+        A r = M::get(p[0]);
+        for (int h = 1; h < H; ++h) r = M::op(r, M::get(p[h]));
+        if (R) R[x1 * n2 + x2] = M::template put<C>(r);
+        tot = M::op(tot, r);
+    }
+    tot = block_reduce<M>(tot, red);
+    if (threadIdx.x == 0) R2[x1] = M::template put<C>(tot);
+}
+
+// ---------------------------------------------------------------------------
+// Excluded sums of the n1 x n2 tensor R with box (k1, k2), given its plane
+// totals R2 (one block per x1, k1 <= 64, n2 <= 4096; dynamic shared memory
+// 2 * n2 accumulators):
+//   T2  = (+)_{y < x1} R2[y] (+) (+)_{y >= x1 + k1} R2[y]
+//   H1  = (+)_{i < k1, x1 + i < n1} R[x1 + i, .]         (window of planes)
+//   T[x1, x2] = T2 (+) exclusive prefix of H1 before x2 (+) suffix of H1 from x2 + k2
+// The scans along x2: each thread scans a contiguous segment, the segment
+// totals are scanned across the block (warp shuffles, then the warp totals),
+// in both directions.
+// ---------------------------------------------------------------------------
+template <class M>
+__global__ void __launch_bounds__(256)
+k_exc2d(const typename M::car_t *__restrict__ R, const typename M::car_t *__restrict__ R2,
+        typename M::car_t *__restrict__ T, int n1, int n2, int k1, int k2)
+{
+    using A = typename M::acc_t;
+    using C = typename M::car_t;
+    extern __shared__ __align__(16) unsigned char e2_smem[];
+    A *hv = reinterpret_cast<A *>(e2_smem);   // H1, then its exclusive prefixes
+    A *sf = hv + n2;                            // inclusive suffixes of H1
+    __shared__ A red[33];
+    __shared__ A wpre[32], wsuf[32];
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    const int x1 = blockIdx.x;
+    // the one-dimensional part
+    A t2 = M::id();
+    for (int y = tid; y < n1; y += nt)
+        if (y < x1 || y >= x1 + k1) t2 = M::op(t2, M::get(R2[y]));
+    t2 = block_reduce<M>(t2, red);
+    // window of k1 planes
+    const int kw = min(k1, n1 - x1);
+    for (int x2 = tid; x2 < n2; x2 += nt) {
+        const C *col = R + (int64_t)x1 * n2 + x2;
+        A h = M::get(col[0]);
+        for (int i = 1; i < kw; ++i) h = M::op(h, M::get(col[(int64_t)i * n2]));
+        hv[x2] = h;
+    }
+    __syncthreads();
+    // scans along x2: thread segment [s0, s1)
+    const int seg = (n2 + nt - 1) / nt;
+    const int s0 = min(tid * seg, n2), s1 = min(s0 + seg, n2);
+    A st = M::id();
+    for (int x = s0; x < s1; ++x) st = M::op(st, hv[x]);
+    // exclusive prefix and exclusive suffix of the segment totals
+    A pi = st, si = st;
+#pragma unroll
+    for (int dl = 1; dl < 32; dl <<= 1) {
+        const A u = shfl_up(pi, dl);
+        const A w = shfl_down(si, dl);
+        if (lane >= dl) pi = M::op(u, pi);
+        if (lane + dl < 32) si = M::op(si, w);
+    }
+    if (lane == 31) wpre[warp] = pi;
+    if (lane == 0) wsuf[warp] = si;
+    __syncthreads();
+    A pw = M::id(), sw = M::id();
+    for (int w = 0; w < warp; ++w) pw = M::op(pw, wpre[w]);
+    for (int w = nw - 1; w > warp; --w) sw = M::op(wsuf[w], sw);
+    A pe = shfl_up(pi, 1), se = shfl_down(si, 1);
+    if (lane == 0) pe = M::id();
+    if (lane == 31) se = M::id();
+    pe = M::op(pw, pe);
+    se = M::op(se, sw);
+    // suffixes (backwards) and exclusive prefixes (forwards, in place)
+    A run = se;
+    for (int x = s1 - 1; x >= s0; --x) {
+        run = M::op(hv[x], run);
+        sf[x] = run;
+    }
+    run = pe;
+    for (int x = s0; x < s1; ++x) {
+        const A h = hv[x];
+        hv[x] = run;
+        run = M::op(run, h);
+    }
+    __syncthreads();
+    for (int x2 = tid; x2 < n2; x2 += nt) {
+        const A s = x2 + k2 < n2 ? sf[x2 + k2] : M::id();
+        T[(int64_t)x1 * n2 + x2] = M::template put<C>(M::op(t2, M::op(hv[x2], s)));
+    }
+}
+
+}  // namespace exsum

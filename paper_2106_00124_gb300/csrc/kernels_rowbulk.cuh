@@ -146,9 +146,13 @@ __host__ __device__ inline size_t rowbulk_smem(int TR, int k2, bool aligned, int
 
 // Window walk of one column group of CW adjacent elements over output rows
 // [s0, s1) of a tile: reads the staging buffer (rows L apart, unswizzled),
-// writes the swizzled row buffer W (rows LSW apart).  FULL: k == KMAX and
-// s1 - s0 a multiple of k, so every load and store is unconditional (rows
-// up to s1 + k - 2 are read).
+// writes the swizzled row buffer W (rows LSW apart).
+//
+// FULL (k == KMAX, s1 - s0 a multiple of k): blocks of k rows, each output
+// the suffix of its block from the row on plus the prefix of the next block
+// up to the row before its window ends -- 3k - 4 operations per column and
+// block, every load and store unconditional; rows up to s1 + k - 2 are read.
+// Otherwise the generic walk with runtime k <= KMAX (identity padding).
 template <class M, int KMAX, int CW, bool FULL>
 __device__ __forceinline__ void rowbulk_walk(const typename M::loc_t *__restrict__ st,
                                              typename M::loc_t *__restrict__ W, int L, int LSW, int c0,
@@ -156,9 +160,8 @@ __device__ __forceinline__ void rowbulk_walk(const typename M::loc_t *__restrict
 {
     using Lt = typename M::loc_t;
     using V = typename std::conditional<CW == 4, uint4, typename std::conditional<CW == 2, uint2, uint32_t>::type>::type;
-    const int wc = tswz<Lt>(c0);
     const Lt *sp = st + c0;
-    Lt *wp = W + wc;
+    Lt *wp = W + tswz<Lt>(c0);
     auto ld = [&](int r, Lt *v) {
         const V w = *reinterpret_cast<const V *>(sp + r * L);
         memcpy(v, &w, sizeof(V));
@@ -174,11 +177,49 @@ __device__ __forceinline__ void rowbulk_walk(const typename M::loc_t *__restrict
             ld(r, v);
             stw(r, v);
         }
+    } else if constexpr (FULL) {
+        constexpr int K = KMAX;
+        Lt cur[K][CW];
+#pragma unroll
+        for (int j = 0; j < K; ++j) ld(s0 + j, cur[j]);
+        for (int sb = s0; sb < s1; sb += K) {
+            // suffixes of the current block, in place
+#pragma unroll
+            for (int j = K - 2; j >= 0; --j)
+#pragma unroll
+                for (int c = 0; c < CW; ++c) cur[j][c] = M::lop(cur[j][c], cur[j + 1][c]);
+            stw(sb, cur[0]);
+            const bool more = sb + K < s1;
+            Lt nx[K][CW];
+#pragma unroll
+            for (int j = 0; j < K - 1; ++j) ld(sb + K + j, nx[j]);
+            if (more) ld(sb + 2 * K - 1, nx[K - 1]);
+            Lt p[CW], o[CW];
+#pragma unroll
+            for (int c = 0; c < CW; ++c) {
+                p[c] = nx[0][c];
+                o[c] = M::lop(cur[1][c], p[c]);
+            }
+            stw(sb + 1, o);
+#pragma unroll
+            for (int j = 1; j + 1 < K; ++j) {
+#pragma unroll
+                for (int c = 0; c < CW; ++c) {
+                    p[c] = M::lop(p[c], nx[j][c]);
+                    o[c] = M::lop(cur[j + 1][c], p[c]);
+                }
+                stw(sb + 1 + j, o);
+            }
+#pragma unroll
+            for (int j = 0; j < K; ++j)
+#pragma unroll
+                for (int c = 0; c < CW; ++c) cur[j][c] = nx[j][c];
+        }
     } else {
         Lt S[KMAX][CW], v[KMAX][CW];
 #pragma unroll
         for (int j = 0; j < KMAX; ++j) {
-            if (FULL || j < k) {
+            if (j < k) {
                 ld(s0 + j, v[j]);
             } else {
 #pragma unroll
@@ -191,13 +232,12 @@ __device__ __forceinline__ void rowbulk_walk(const typename M::loc_t *__restrict
         for (int j = KMAX - 2; j >= 0; --j)
 #pragma unroll
             for (int c = 0; c < CW; ++c) S[j][c] = M::lop(v[j][c], S[j + 1][c]);
-        const int kk = FULL ? KMAX : k;
-        for (int sb = s0; sb < s1; sb += kk) {
+        for (int sb = s0; sb < s1; sb += k) {
             stw(sb, S[0]);
-            const int nb = sb + kk;
+            const int nb = sb + k;
 #pragma unroll
             for (int j = 0; j < KMAX; ++j) {
-                if (FULL || j < k) {
+                if (j < k) {
                     ld(nb + j, v[j]);
                 } else {
 #pragma unroll
@@ -206,16 +246,16 @@ __device__ __forceinline__ void rowbulk_walk(const typename M::loc_t *__restrict
             }
             Lt p[CW];
 #pragma unroll
-            for (int c = 0; c < CW; ++c) p[c] = M::lid();
+            for (int c = 0; c < CW; ++c) p[c] = v[0][c];
 #pragma unroll
             for (int j = 0; j + 1 < KMAX; ++j) {
                 Lt o[CW];
 #pragma unroll
                 for (int c = 0; c < CW; ++c) {
-                    p[c] = M::lop(p[c], v[j][c]);
+                    if (j > 0) p[c] = M::lop(p[c], v[j][c]);
                     o[c] = M::lop(S[j + 1][c], p[c]);
                 }
-                if (FULL || (j + 1 < k && sb + 1 + j < s1)) stw(sb + 1 + j, o);
+                if (j + 1 < k && sb + 1 + j < s1) stw(sb + 1 + j, o);
             }
 #pragma unroll
             for (int c = 0; c < CW; ++c) S[KMAX - 1][c] = v[KMAX - 1][c];
@@ -234,18 +274,24 @@ __device__ __forceinline__ void rowbulk_walk(const typename M::loc_t *__restrict
 // LP rounded up to 32, k2 <= KMAX, TR a multiple of (NT / 32) * (32 / lpr)
 // (the rows one pass of the row phase covers), ntiles < 2^31, smem =
 // rowbulk_smem(...).  `aligned` (k2 == KMAX and TR a multiple of the
-// walk's segments times k2) selects the bounds-free walk.  Tile t covers
-// rows [a, a + TR) of slice t / ntile, a = (t % ntile) * TR.  One lane waits
+// walk's segments times k2) selects the bounds-free walk.  LT > 0 fixes the
+// row length at compile time (then L == LT, EPL * lpr == LT, LSW == LT and
+// the walk must be aligned), so that strides and offsets are immediates.
+// Tile t covers rows [a, a + TR) of slice t / ntile, a = (t % ntile) * TR;
+// a block advances its tile coordinates without dividing.  One lane waits
 // for each copy (suspending, bounded); a block barrier releases the others.
 // A block that gives up waiting counts itself in g_wait_timeouts and
 // returns (never expected).
 // ---------------------------------------------------------------------------
-template <class M, class SOut, int KMAX, int EPL, int NBUF, int NT>
+template <class M, class SOut, int KMAX, int EPL, int NBUF, int NT, int LT>
 __global__ void __launch_bounds__(NT, 512 / NT)
 k_rowx_bulk(const typename M::loc_t *__restrict__ in, const typename M::car_t *__restrict__ T,
-            SOut *__restrict__ out, int ntiles, int ntile, int n2, int L, int k2, int k3, int TR,
-            int LSW, int lpr, int aligned)
+            SOut *__restrict__ out, int ntiles, int ntile, int n2, int L_, int k2, int k3, int TR,
+            int LSW_, int lpr_, int aligned)
 {
+    const int L = LT > 0 ? LT : L_;
+    const int LSW = LT > 0 ? LT : LSW_;
+    const int lpr = LT > 0 ? LT / EPL : lpr_;
     using Lt = typename M::loc_t;
     using A = typename M::acc_t;
     static_assert(sizeof(Lt) == 4 && sizeof(SOut) == 4, "4-byte local and output types");
@@ -253,7 +299,7 @@ k_rowx_bulk(const typename M::loc_t *__restrict__ in, const typename M::car_t *_
     constexpr int NW = NT / 32;
     extern __shared__ __align__(128) unsigned char rb_smem[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(rb_smem);
-    const bool al = aligned != 0;
+    const bool al = LT > 0 || aligned != 0;
     const int RSA = rowbulk_stage_rows(TR, k2, al);
     Lt *stage0 = reinterpret_cast<Lt *>(rb_smem + 128);
     Lt *W = stage0 + NBUF * RSA * L;
@@ -268,8 +314,9 @@ k_rowx_bulk(const typename M::loc_t *__restrict__ in, const typename M::car_t *_
 
     // ---- one-time set-up: identity that no tile overwrites ----
     if (tid < 4) idc[tid] = M::lid();
-    // W: columns [L, LP) of every row (strip padding of the row phase)
-    if (LP > L) {
+    // W: columns [L, LP) of every row (strip padding of the row phase;
+    // none when the row length is fixed at compile time)
+    if (LT == 0 && LP > L) {
         const int padw = LP - L;
         for (int i = tid; i < TR * padw; i += NT) {
             const int r = i / padw;
@@ -301,9 +348,7 @@ k_rowx_bulk(const typename M::loc_t *__restrict__ in, const typename M::car_t *_
     // Stages tile t into buffer b: identity in rows [nst, TR + halo) first
     // (all threads; ordered before the walk by the barriers in between),
     // then one bulk copy by thread 0.
-    auto issue = [&](int t, int b) {
-        const int o = t / ntile;
-        const int a = (t - o * ntile) * TR;
+    auto issue = [&](int o, int a, int b) {
         const int nst = min(TR + halo, n2 - a);
         Lt *st = stage0 + b * RSA * L;
         for (int i = tid; i < (TR + halo - nst) * L; i += NT) st[nst * L + i] = M::lid();
@@ -320,8 +365,24 @@ k_rowx_bulk(const typename M::loc_t *__restrict__ in, const typename M::car_t *_
         mbar_fence_init();
     }
     __syncthreads();
-    for (int b = 0; b < NBUF; ++b)
-        if ((int)blockIdx.x + b * grid < ntiles) issue((int)blockIdx.x + b * grid, b);
+    // tile coordinates (slice, tile in slice) of this block's current tile
+    // and of the next tile to stage; a step of `grid` tiles is (go, gj)
+    const int go = grid / ntile, gj = grid - go * ntile;
+    int o_cur = (int)blockIdx.x / ntile;
+    int j_cur = (int)blockIdx.x - o_cur * ntile;
+    int o_nx = o_cur, j_nx = j_cur;
+    auto step = [&](int &oo, int &jj) {
+        oo += go;
+        jj += gj;
+        if (jj >= ntile) {
+            jj -= ntile;
+            ++oo;
+        }
+    };
+    for (int b = 0; b < NBUF; ++b) {
+        if ((int)blockIdx.x + b * grid < ntiles) issue(o_nx, j_nx * TR, b);
+        step(o_nx, j_nx);
+    }
 
     // Row-phase constants: lane `sub` of a row owns strip [e0, e0 + EPL).
     const int sub = lane & (lpr - 1);
@@ -332,13 +393,25 @@ k_rowx_bulk(const typename M::loc_t *__restrict__ in, const typename M::car_t *_
     for (int i = 0; i < EPL / 4; ++i) toff[i] = tswz<Lt>(e0 + 4 * i);
     const bool vsb = (k3 & 3) == 0;
     const int L4 = L >> 2;
+    // shifted-suffix chunk of strip chunk i: e0 + 4 i + k3 (vector path),
+    // -1 past the row end (identity)
+    int soff[EPL / 4];
+#pragma unroll
+    for (int i = 0; i < EPL / 4; ++i) {
+        const int js = e0 + 4 * i + k3;
+        soff[i] = js < L ? tswz<Lt>(js) : -1;
+    }
+    // copy-out: lane reads chunk c = lane + 32 j of a row; its swizzled
+    // offset is 128 j + 4 (lane ^ ((lane >> 3) + 4 (j & 1)))
+    const int coff_e = 4 * (lane ^ (lane >> 3));
+    const int coff_o = 4 * (lane ^ ((lane >> 3) + 4));
 
     int it = 0;
-    for (int t = blockIdx.x; t < ntiles; t += grid, ++it) {
+    for (int t = blockIdx.x; t < ntiles; t += grid, ++it, step(o_cur, j_cur)) {
         const int b = NBUF == 1 ? 0 : it % NBUF;
         const unsigned parity = (unsigned)(it / NBUF) & 1u;
-        const int o = t / ntile;
-        const int a = (t - o * ntile) * TR;
+        const int o = o_cur;
+        const int a = j_cur * TR;
         const int nout = min(TR, n2 - a);
         const Lt *stage = stage0 + b * RSA * L;
         int ok = 1;
@@ -362,7 +435,8 @@ k_rowx_bulk(const typename M::loc_t *__restrict__ in, const typename M::car_t *_
         }
         __syncthreads();
         // the staging buffer is free: stage a later tile under the row phase
-        if (t + NBUF * grid < ntiles) issue(t + NBUF * grid, b);
+        if (t + NBUF * grid < ntiles) issue(o_nx, j_nx * TR, b);
+        step(o_nx, j_nx);
 
         // ---- rows: T (+) exclusive prefix (+) suffix from x_d + k3 ----
         const int64_t rowbase = (int64_t)o * n2 + a;
@@ -418,8 +492,7 @@ k_rowx_bulk(const typename M::loc_t *__restrict__ in, const typename M::car_t *_
             if (vsb) {
 #pragma unroll
                 for (int i = 0; i < EPL / 4; ++i) {
-                    const int js = e0 + 4 * i + k3;
-                    const Lt *q = js < L ? row + tswz<Lt>(js) : idc;
+                    const Lt *q = soff[i] >= 0 ? row + soff[i] : idc;
                     const uint4 w = *reinterpret_cast<const uint4 *>(q);
                     Lt sv[4];
                     memcpy(sv, &w, 16);
@@ -453,10 +526,13 @@ k_rowx_bulk(const typename M::loc_t *__restrict__ in, const typename M::car_t *_
                 const int rr = rb + q;
                 if (rr >= nout) break;
                 const Lt *src = W + rr * LSW;
-                SOut *dst = out + (rowbase + rr) * (int64_t)L;
-                for (int c = lane; c < L4; c += 32) {
-                    const uint4 w = *reinterpret_cast<const uint4 *>(src + tswz<Lt>(4 * c));
-                    st_hint_v4(dst + 4 * c, w, pol_out);
+                SOut *dst = out + (rowbase + rr) * (int64_t)L + 4 * lane;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    if (lane + 32 * j < L4) {
+                        const uint4 w = *reinterpret_cast<const uint4 *>(src + 128 * j + ((j & 1) ? coff_o : coff_e));
+                        st_hint_v4(dst + 128 * j, w, pol_out);
+                    }
                 }
             }
         }

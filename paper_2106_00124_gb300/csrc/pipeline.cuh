@@ -15,6 +15,7 @@
 #include <type_traits>
 
 #include "kernels_flat.cuh"
+#include "kernels_fold.cuh"
 #include "kernels_rowbulk.cuh"
 #include "kernels_rows.cuh"
 
@@ -35,7 +36,10 @@ enum KernelTag {
     TAG_ROWSUM = 7,       // row totals over the last dimension (k_row_totals)
     TAG_ROWX = 8,         // last-dimension prefix/suffix + contributions (k_rowx)
     TAG_WEAK = 9,         // weak excluded sums: total, then total minus included
-    TAG_COUNT = 10
+    TAG_INC_FOLD = 10,    // BDBS-Along-Dim, strided, with partial row totals (k_inc_strided4_rt)
+    TAG_PLANE = 11,       // plane totals of the two-dimensional lower problem (k_plane_totals)
+    TAG_EXC2D = 12,       // excluded sums of the two-dimensional lower problem (k_exc2d)
+    TAG_COUNT = 13
 };
 
 // Launch bracketing for the trace and the launch counter (exsum_abi.cu).
@@ -472,8 +476,8 @@ struct Pipe {
         if ((int64_t)lpr * epl < L) return bp;
         const int LP = lpr * epl;
         const int LSW = (LP + 31) & ~31;
-        const int nt = env_int("EXSUM_ROWX_NT", 256) == 512 ? 512 : 256;
-        const int nbuf = env_int("EXSUM_ROWX_NBUF", 2) == 1 ? 1 : 2;
+        const int nt = 256;
+        const int nb_env = env_int("EXSUM_ROWX_NBUF", 0);
         const int rows_pass = (nt / 32) * (32 / lpr);
         const int G = rowbulk_segs((int)L, kmax, nt);
         int step = rows_pass;
@@ -482,27 +486,32 @@ struct Pipe {
         if (kfull)
             while ((step / G) % kk) step += rows_pass;
         const int tr_env = env_int("EXSUM_ROWX_TR", 0);
-        auto sm = [&](int tr) {
+        auto sm = [&](int tr, int nb) {
             const bool al = kfull && (tr / G) % kk == 0 && tr % G == 0;
-            return rowbulk_smem(tr, kk, al, (int)L, LSW, nbuf);
+            return rowbulk_smem(tr, kk, al, (int)L, LSW, nb);
         };
         const size_t two = 113 * 1024, one = 226 * 1024;
-        int TR = 0, bps = nt == 512 ? 1 : 2;
-        if (tr_env > 0) {
-            TR = (tr_env + step - 1) / step * step;
-            if (sm(TR) > two) bps = 1;
-        } else {
-            const size_t lim = bps == 2 ? two : one;
-            for (int tr = (64 / step) * step; tr >= step && !TR; tr -= step)
-                if (sm(tr) <= lim) TR = tr;
-            if (!TR && bps == 2) {
-                bps = 1;
+        // candidates in order of preference: (staging buffers, blocks per SM)
+        const int cand[3][2] = {{2, 2}, {1, 2}, {1, 1}};
+        int TR = 0, nbuf = 1, bps = 2;
+        for (int c = 0; c < 3 && !TR; ++c) {
+            const int nb = cand[c][0];
+            if (nb_env && nb != nb_env) continue;
+            const size_t lim = cand[c][1] == 2 ? two : one;
+            if (tr_env > 0) {
+                const int tr = (tr_env + step - 1) / step * step;
+                if (sm(tr, nb) <= lim) TR = tr;
+            } else {
                 for (int tr = (64 / step) * step; tr >= step && !TR; tr -= step)
-                    if (sm(tr) <= one) TR = tr;
+                    if (sm(tr, nb) <= lim) TR = tr;
+            }
+            if (TR) {
+                nbuf = nb;
+                bps = cand[c][1];
             }
         }
         if (!TR) return bp;
-        const size_t smem = sm(TR);
+        const size_t smem = sm(TR, nbuf);
         if (smem > one) return bp;
         const int64_t ntile = cdiv(n2, TR);
         if (O2 * ntile >= (1ll << 31)) return bp;
@@ -521,11 +530,11 @@ struct Pipe {
         return bp;
     }
 
-    template <class SOut, int KM, int EPL, int NB, int NT>
+    template <class SOut, int KM, int EPL, int NB, int NT, int LT = 0>
     static void rowbulk_go(Ctx &cx, const BulkPlan &bp, const L_ *src, const CAR *T, SOut *out,
                            int64_t n2, int64_t L, int kk, int k3)
     {
-        auto kern = k_rowx_bulk<M, SOut, KM, EPL, NB, NT>;
+        auto kern = k_rowx_bulk<M, SOut, KM, EPL, NB, NT, LT>;
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bp.smem);
         kern<<<(unsigned)bp.grid, NT, bp.smem, cx.stream>>>(src, T, out, bp.ntiles, bp.ntile, (int)n2,
                                                             (int)L, kk, k3, bp.TR, bp.LSW, bp.lpr,
@@ -536,9 +545,30 @@ struct Pipe {
     static void rowbulk_epl(Ctx &cx, const BulkPlan &bp, const L_ *src, const CAR *T, SOut *out,
                             int64_t n2, int64_t L, int kk, int k3)
     {
-        if (bp.nt == 512)
-            rowbulk_go<SOut, KM, 32, 2, 512>(cx, bp, src, T, out, n2, L, kk, k3);
-        else if (bp.nbuf == 1)
+        // row lengths fixed at compile time for the common block-aligned cases
+        if constexpr (KM == 4 || KM == 8) {
+            if (bp.nt == 256 && bp.aligned && bp.LSW == L && bp.lpr * bp.epl == L) {
+                if (L == 256 && bp.epl == 32) {
+                    if (bp.nbuf == 2)
+                        rowbulk_go<SOut, KM, 32, 2, 256, 256>(cx, bp, src, T, out, n2, L, kk, k3);
+                    else
+                        rowbulk_go<SOut, KM, 32, 1, 256, 256>(cx, bp, src, T, out, n2, L, kk, k3);
+                    return;
+                }
+                if (L == 512 && bp.epl == 32) {
+                    if (bp.nbuf == 2)
+                        rowbulk_go<SOut, KM, 32, 2, 256, 512>(cx, bp, src, T, out, n2, L, kk, k3);
+                    else
+                        rowbulk_go<SOut, KM, 32, 1, 256, 512>(cx, bp, src, T, out, n2, L, kk, k3);
+                    return;
+                }
+                if (L == 128 && bp.epl == 16 && bp.nbuf == 2) {
+                    rowbulk_go<SOut, KM, 16, 2, 256, 128>(cx, bp, src, T, out, n2, L, kk, k3);
+                    return;
+                }
+            }
+        }
+        if (bp.nbuf == 1)
             rowbulk_go<SOut, KM, 32, 1, 256>(cx, bp, src, T, out, n2, L, kk, k3);
         else if (bp.epl == 16)
             rowbulk_go<SOut, KM, 16, 2, 256>(cx, bp, src, T, out, n2, L, kk, k3);
@@ -559,8 +589,7 @@ struct Pipe {
             const int kmax = kk <= 1 ? 1 : kk <= 4 ? 4 : kk <= 8 ? 8 : kk <= 16 ? 16 : 32;
             BulkPlan bp = bulk_plan(L, n2, O2, kk, kmax, cx.sms);
             if (!bp.ok) return false;
-            if (bp.nt == 512 && bp.epl != 32) return false;
-            if (bp.nbuf == 1 && bp.epl != 32) return false;
+            if (bp.nt != 256 || (bp.nbuf == 1 && bp.epl != 32)) return false;
             if (kmax == 1)
                 rowbulk_epl<SOut, 1>(cx, bp, src, T, out, n2, L, 1, k3);
             else if (kmax == 4)
@@ -604,6 +633,52 @@ struct Pipe {
     }
 
 
+    // The first strided pass (dimension 1, view [n1, I]) with partial row
+    // totals Rp (kernels_fold.cuh).
+    template <class SIn, class SOut>
+    static void fold_pass(Ctx &cx, const SIn *src, SOut *dst, int64_t n1, int64_t I, int64_t k1, int64_t L,
+                          L_ *Rp)
+    {
+        if constexpr (sizeof(L_) == 4 && sizeof(SOut) == 4) {
+            int Lc = 128;
+            while (Lc > 2 * k1 && Lc > 16 && cdiv(n1, Lc) * (I / 4) < cx.sms * 1024) Lc >>= 1;
+            if (Lc > 32) Lc = 32;
+            if (Lc > n1) Lc = (int)n1;
+            const int nchunks = (int)cdiv(n1, Lc);
+            const int64_t total = nchunks * (I / 4);
+            cx.before(TAG_INC_FOLD, n1 * I);
+            if (k1 <= 4)
+                k_inc_strided4_rt<M, SIn, SOut, 4><<<(unsigned)cdiv(total, 128), 128, 0, cx.stream>>>(
+                    src, dst, (int)n1, I, (int)k1, Lc, nchunks, (int)L, Rp);
+            else
+                k_inc_strided4_rt<M, SIn, SOut, 8><<<(unsigned)cdiv(total, 128), 128, 0, cx.stream>>>(
+                    src, dst, (int)n1, I, (int)k1, Lc, nchunks, (int)L, Rp);
+            cx.check_launch();
+        }
+    }
+
+    // The two-dimensional lower problem T = excluded(R, (k1, k2)) of an
+    // [n1, n2] tensor of row totals: plane totals R2 (from the H partials
+    // of each row in P, writing R too, or from R itself with P == R, H == 1
+    // and Rw null), then one block per plane (kernels_fold.cuh).
+    template <class SP>
+    static void lower2d(Ctx &cx, const SP *P, int H, CAR *Rw, const CAR *R, CAR *R2, CAR *T, int64_t n1,
+                        int64_t n2, int64_t k1, int64_t k2)
+    {
+        if (cx.dry || !cx.ok()) return;
+        cx.level++;
+        cx.before(TAG_PLANE, n1 * n2);
+        k_plane_totals<MC, SP><<<(unsigned)n1, 256, 0, cx.stream>>>(P, H, Rw, R2, (int)n2);
+        cx.check_launch();
+        const size_t smem = 2 * (size_t)n2 * sizeof(typename MC::acc_t);
+        auto kern = k_exc2d<MC>;
+        if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cx.before(TAG_EXC2D, n1 * n2);
+        kern<<<(unsigned)n1, 256, smem, cx.stream>>>(R, R2, T, (int)n1, (int)n2, (int)k1, (int)k2);
+        cx.check_launch();
+        cx.level--;
+    }
+
     template <class SIn, class SOut>
     static void excluded_rows(Ctx &cx, const RowPlan &rp, const SIn *X, SOut *out, int d,
                               const int64_t *n, const int64_t *k)
@@ -622,6 +697,44 @@ struct Pipe {
         SOut *B2 = P > 1 ? cx.take<SOut>(N) : nullptr;
         CAR *R = cx.take<CAR>(rows);
         CAR *T = cx.take<CAR>(rows);
+        // d = 3: the lower problem is two-dimensional and, for boxes k1 <= 64
+        // and planes of at most 4096 rows, takes two short kernels.  When the
+        // first pass is the 16-byte strided pass along dimension 1 over rows
+        // of whole 128-element groups, it also leaves partial row totals, and
+        // X is read once instead of twice (kernels_fold.cuh).
+        const bool lower2 = d == 3 && n[1] <= 4096 && k[0] <= 64 && n[0] < (1ll << 31);
+        bool fold = false;
+        if constexpr (sizeof(L_) == 4 && sizeof(SOut) == 4)
+            fold = lower2 && P > 0 && dims[0] == 0 && (L % 128) == 0 && k[0] <= 8 &&
+                   env_int("EXSUM_FOLD", 1) != 0;
+        CAR *R2 = lower2 ? cx.take<CAR>(n[0]) : nullptr;
+        L_ *Rp = fold ? cx.take<L_>(rows * (L / 128)) : nullptr;
+        if (fold && !cx.dry && cx.ok()) {
+            SOut *dst0 = ((P - 1) % 2 == 0) ? B : B2;
+            if ((((uintptr_t)X) & (sizeof(SIn) * 4 - 1)) || (((uintptr_t)dst0) & 15)) fold = false;
+        }
+        if (fold) {
+            // everything on the caller's stream: pass 1 (+ partial row
+            // totals) -> plane totals -> lower excluded sums -> final pass
+            if (cx.dry || !cx.ok()) return;
+            SOut *dst0 = ((P - 1) % 2 == 0) ? B : B2;
+            int64_t I = N / n[0];
+            fold_pass<SIn, SOut>(cx, X, dst0, n[0], I, k[0], L, Rp);
+            lower2d<L_>(cx, Rp, (int)(L / 128), R, R, R2, T, n[0], n[1], k[0], k[1]);
+            const void *cur = dst0;
+            for (int p = 1; p < P; ++p) {
+                const int j = dims[p];
+                int64_t O = 1;
+                I = 1;
+                for (int m = 0; m < j; ++m) O *= n[m];
+                for (int m = j + 1; m < d; ++m) I *= n[m];
+                SOut *dst = ((P - 1 - p) % 2 == 0) ? B : B2;
+                inc_pass<SOut, SOut>(cx, (const SOut *)cur, dst, O, n[j], I, k[j]);
+                cur = dst;
+            }
+            rowx_launch<SOut, SOut>(cx, rp, (const SOut *)cur, T, nullptr, out, O2, n2, L, k[d - 2], k[d - 1]);
+            return;
+        }
         // Row totals and the lower-dimensional recursion run on the side
         // stream while the BDBS passes run on the caller's.  A one-dimensional
         // recursion of at most ROWX_TAIL elements is left to the final pass
@@ -651,7 +764,9 @@ struct Pipe {
                 k_row_totals<M, SIn, 32><<<(unsigned)blocks, 256, 0, cx.stream>>>(X, R, rows, (int)L);
             cx.check_launch();
         }
-        if (!tail) {
+        if (lower2) {
+            lower2d<CAR>(cx, R, 1, nullptr, R, R2, T, n[0], n[1], k[0], k[1]);
+        } else if (!tail) {
             cx.level++;
             Pipe<MC>::template excluded<CAR, CAR>(cx, R, T, d - 1, n, k);
             cx.level--;
