@@ -42,6 +42,7 @@ k_inc_strided4_rt(const SIn *__restrict__ in, SOut *__restrict__ out, int n, int
     const int64_t I4 = I >> 2;
     const int64_t total = nchunks * I4;
     const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    pdl_trigger();   // the plane totals may launch (they wait for this grid)
     if (gid >= total) return;   // whole warps: total is a multiple of 32
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t i4 = gid % I4;
@@ -161,11 +162,20 @@ k_plane_totals(const SP *__restrict__ P, int H, typename M::car_t *__restrict__ 
     using C = typename M::car_t;
     __shared__ A red[33];
     const int64_t x1 = blockIdx.x;
+    pdl_trigger();
+    pdl_wait();   // P comes from the kernel before
     A tot = M::id();
     for (int x2 = threadIdx.x; x2 < n2; x2 += blockDim.x) {
         const SP *p = P + (x1 * n2 + x2) * H;
-        A r = M::get(p[0]);
-        for (int h = 1; h < H; ++h) r = M::op(r, M::get(p[h]));
+        // H <= 8: all loads issued before the first use
+        SP v[8];
+#pragma unroll
+        for (int h = 0; h < 8; ++h)
+            if (h < H) v[h] = p[h];
+        A r = M::get(v[0]);
+#pragma unroll
+        for (int h = 1; h < 8; ++h)
+            if (h < H) r = M::op(r, M::get(v[h]));
         if (R) R[x1 * n2 + x2] = M::template put<C>(r);
         tot = M::op(tot, r);
     }
@@ -198,17 +208,39 @@ k_exc2d(const typename M::car_t *__restrict__ R, const typename M::car_t *__rest
     __shared__ A wpre[32], wsuf[32];
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
     const int x1 = blockIdx.x;
+    pdl_trigger();
+    pdl_wait();   // R and R2 come from the kernel before
     // the one-dimensional part
     A t2 = M::id();
-    for (int y = tid; y < n1; y += nt)
-        if (y < x1 || y >= x1 + k1) t2 = M::op(t2, M::get(R2[y]));
+    for (int y0 = 0; y0 < n1; y0 += 4 * nt) {
+        C v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int y = y0 + u * nt + tid;
+            v[u] = y < n1 ? R2[y] : M::template put<C>(M::id());
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int y = y0 + u * nt + tid;
+            if (y < n1 && (y < x1 || y >= x1 + k1)) t2 = M::op(t2, M::get(v[u]));
+        }
+    }
     t2 = block_reduce<M>(t2, red);
     // window of k1 planes
     const int kw = min(k1, n1 - x1);
     for (int x2 = tid; x2 < n2; x2 += nt) {
         const C *col = R + (int64_t)x1 * n2 + x2;
         A h = M::get(col[0]);
-        for (int i = 1; i < kw; ++i) h = M::op(h, M::get(col[(int64_t)i * n2]));
+        // eight loads in flight per round
+        for (int i0 = 1; i0 < kw; i0 += 8) {
+            C v[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                if (i0 + i < kw) v[i] = col[(int64_t)(i0 + i) * n2];
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                if (i0 + i < kw) h = M::op(h, M::get(v[i]));
+        }
         hv[x2] = h;
     }
     __syncthreads();

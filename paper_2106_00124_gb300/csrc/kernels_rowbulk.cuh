@@ -364,6 +364,9 @@ k_rowx_bulk(const typename M::loc_t *__restrict__ in, const typename M::car_t *_
         for (int b = 0; b < NBUF; ++b) mbar_init(bar + b, 1);
         mbar_fence_init();
     }
+    // Everything above is private set-up; the input and T may come from the
+    // kernels before this one (programmatic dependent launch).
+    pdl_wait();
     __syncthreads();
     // tile coordinates (slice, tile in slice) of this block's current tile
     // and of the next tile to stage; a step of `grid` tiles is (go, gj)

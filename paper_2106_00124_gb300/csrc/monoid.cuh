@@ -296,6 +296,16 @@ __device__ __forceinline__ void st_hint_v4(void *p, uint4 r, uint64_t pol)
                  : "memory");
 }
 
+// --- programmatic dependent launch -------------------------------------------------------
+// A kernel launched with programmatic stream serialization may start while
+// the kernel before it on the stream is still running.  pdl_wait() returns
+// once that kernel has completed and its memory is visible; every read of
+// its results (and every write to memory it reads) comes after it.
+// pdl_trigger() lets the next such kernel launch before this one ends.
+// Both are no-ops for a kernel launched normally.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+
 // --- warp shuffles of accumulator values ---------------------------------------------
 __device__ __forceinline__ int32_t shfl_up(int32_t v, int dl) { return __shfl_up_sync(0xffffffffu, v, dl); }
 __device__ __forceinline__ int64_t shfl_up(int64_t v, int dl)

@@ -90,6 +90,27 @@ struct Ctx {
 
 static inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
+// Launches `kern` on `stream` with programmatic stream serialization: it may
+// start while the kernel before it on the stream finishes, and waits for it
+// with pdl_wait() before touching that kernel's results.  Launch latency of
+// a chain of short dependent kernels is hidden this way.
+template <class... KArgs, class... Args>
+static inline void launch_pdl(void (*kern)(KArgs...), unsigned grid, unsigned block, size_t smem,
+                              cudaStream_t stream, Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kern, (KArgs)args...);
+}
+
 // Streaming multiprocessors of the current device, looked up once per device
 // (grids and tile heights are sized by it).  Without a usable device (a
 // workspace query on a machine with no GPU) the GB300's 152 is assumed.
@@ -446,7 +467,7 @@ struct Pipe {
 
     // ---- final pass staged by bulk copies (kernels_rowbulk.cuh) ---------------------------
     struct BulkPlan {
-        bool ok = false, aligned = false;
+        bool ok = false, aligned = false, pdl = false;
         int TR = 0, epl = 32, lpr = 8, LSW = 0, nbuf = 2, nt = 256;
         size_t smem = 0;
         int ntiles = 0, grid = 0, ntile = 0;
@@ -536,9 +557,13 @@ struct Pipe {
     {
         auto kern = k_rowx_bulk<M, SOut, KM, EPL, NB, NT, LT>;
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bp.smem);
-        kern<<<(unsigned)bp.grid, NT, bp.smem, cx.stream>>>(src, T, out, bp.ntiles, bp.ntile, (int)n2,
-                                                            (int)L, kk, k3, bp.TR, bp.LSW, bp.lpr,
-                                                            bp.aligned ? 1 : 0);
+        if (bp.pdl)
+            launch_pdl(kern, (unsigned)bp.grid, NT, bp.smem, cx.stream, src, T, out, bp.ntiles, bp.ntile,
+                       (int)n2, (int)L, kk, k3, bp.TR, bp.LSW, bp.lpr, bp.aligned ? 1 : 0);
+        else
+            kern<<<(unsigned)bp.grid, NT, bp.smem, cx.stream>>>(src, T, out, bp.ntiles, bp.ntile, (int)n2,
+                                                                (int)L, kk, k3, bp.TR, bp.LSW, bp.lpr,
+                                                                bp.aligned ? 1 : 0);
     }
 
     template <class SOut, int KM>
@@ -581,7 +606,7 @@ struct Pipe {
     // no one-dimensional tail); returns false otherwise.
     template <class SF, class SOut>
     static bool rowbulk_try(Ctx &cx, const SF *src, const CAR *T, SOut *out, int64_t O2, int64_t n2,
-                            int64_t L, int kk, int k3)
+                            int64_t L, int kk, int k3, bool pdl = false)
     {
         if constexpr (sizeof(L_) == 4 && std::is_same<SF, L_>::value && sizeof(SOut) == 4) {
             if (env_int("EXSUM_ROWX_KERNEL", 1) == 0) return false;
@@ -589,6 +614,7 @@ struct Pipe {
             const int kmax = kk <= 1 ? 1 : kk <= 4 ? 4 : kk <= 8 ? 8 : kk <= 16 ? 16 : 32;
             BulkPlan bp = bulk_plan(L, n2, O2, kk, kmax, cx.sms);
             if (!bp.ok) return false;
+            bp.pdl = pdl;
             if (bp.nt != 256 || (bp.nbuf == 1 && bp.epl != 32)) return false;
             if (kmax == 1)
                 rowbulk_epl<SOut, 1>(cx, bp, src, T, out, n2, L, 1, k3);
@@ -608,14 +634,14 @@ struct Pipe {
 
     template <class SF, class SOut>
     static void rowx_launch(Ctx &cx, const RowPlan &rp, const SF *src, const CAR *T, const CAR *R1, SOut *out,
-                            int64_t O2, int64_t n2, int64_t L, int64_t k2, int64_t k3)
+                            int64_t O2, int64_t n2, int64_t L, int64_t k2, int64_t k3, bool pdl = false)
     {
         if (cx.dry || !cx.ok()) return;
         // the 1-D tail (d == 2) is the excluded sum of R along n2 with box k2
         const int k1 = R1 ? (int)k2 : 0;
         cx.before(TAG_ROWX, O2 * n2 * L);
         const int kk = rp.fuse ? (int)k2 : 1;
-        if (!R1 && rowbulk_try<SF, SOut>(cx, src, T, out, O2, n2, L, kk, (int)k3)) {
+        if (!R1 && rowbulk_try<SF, SOut>(cx, src, T, out, O2, n2, L, kk, (int)k3, pdl)) {
             cx.check_launch();
             return;
         }
@@ -663,18 +689,24 @@ struct Pipe {
     // and Rw null), then one block per plane (kernels_fold.cuh).
     template <class SP>
     static void lower2d(Ctx &cx, const SP *P, int H, CAR *Rw, const CAR *R, CAR *R2, CAR *T, int64_t n1,
-                        int64_t n2, int64_t k1, int64_t k2)
+                        int64_t n2, int64_t k1, int64_t k2, bool pdl = false)
     {
         if (cx.dry || !cx.ok()) return;
         cx.level++;
         cx.before(TAG_PLANE, n1 * n2);
-        k_plane_totals<MC, SP><<<(unsigned)n1, 256, 0, cx.stream>>>(P, H, Rw, R2, (int)n2);
+        if (pdl)
+            launch_pdl(k_plane_totals<MC, SP>, (unsigned)n1, 256, 0, cx.stream, P, H, Rw, R2, (int)n2);
+        else
+            k_plane_totals<MC, SP><<<(unsigned)n1, 256, 0, cx.stream>>>(P, H, Rw, R2, (int)n2);
         cx.check_launch();
         const size_t smem = 2 * (size_t)n2 * sizeof(typename MC::acc_t);
         auto kern = k_exc2d<MC>;
         if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cx.before(TAG_EXC2D, n1 * n2);
-        kern<<<(unsigned)n1, 256, smem, cx.stream>>>(R, R2, T, (int)n1, (int)n2, (int)k1, (int)k2);
+        if (pdl)
+            launch_pdl(kern, (unsigned)n1, 256, smem, cx.stream, R, R2, T, (int)n1, (int)n2, (int)k1, (int)k2);
+        else
+            kern<<<(unsigned)n1, 256, smem, cx.stream>>>(R, R2, T, (int)n1, (int)n2, (int)k1, (int)k2);
         cx.check_launch();
         cx.level--;
     }
@@ -719,8 +751,11 @@ struct Pipe {
             if (cx.dry || !cx.ok()) return;
             SOut *dst0 = ((P - 1) % 2 == 0) ? B : B2;
             int64_t I = N / n[0];
+            // the kernels after the first are launched programmatically
+            // dependent (each waits for the one before; launch latency hidden)
+            const bool pdl = env_int("EXSUM_PDL", 1) != 0;
             fold_pass<SIn, SOut>(cx, X, dst0, n[0], I, k[0], L, Rp);
-            lower2d<L_>(cx, Rp, (int)(L / 128), R, R, R2, T, n[0], n[1], k[0], k[1]);
+            lower2d<L_>(cx, Rp, (int)(L / 128), R, R, R2, T, n[0], n[1], k[0], k[1], pdl);
             const void *cur = dst0;
             for (int p = 1; p < P; ++p) {
                 const int j = dims[p];
@@ -732,7 +767,8 @@ struct Pipe {
                 inc_pass<SOut, SOut>(cx, (const SOut *)cur, dst, O, n[j], I, k[j]);
                 cur = dst;
             }
-            rowx_launch<SOut, SOut>(cx, rp, (const SOut *)cur, T, nullptr, out, O2, n2, L, k[d - 2], k[d - 1]);
+            rowx_launch<SOut, SOut>(cx, rp, (const SOut *)cur, T, nullptr, out, O2, n2, L, k[d - 2], k[d - 1],
+                                    pdl && P == 1);
             return;
         }
         // Row totals and the lower-dimensional recursion run on the side
