@@ -55,6 +55,8 @@ def parse_args(argv=None):
     p.add_argument("--workload", default=DEFAULT_WORKLOAD)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-extras", action="store_true",
+                   help="skip the compact batched and served figures of the default line")
     p.add_argument("--mode", choices=["single", "batched", "served"], default="single",
                    help="single: the default step; batched: 512 uneven tensors as one graph "
                         "launch vs plain per-tensor launches; served: a Poisson request stream "
@@ -308,6 +310,18 @@ def run_ours(args):
         ex.exsum_graph_launch(tgexec, sh)
         torch.cuda.synchronize()
         trace.extend((j,) + rec for j, rec in enumerate(ex.exsum_trace_collect(cap=256, clear=False)))
+    # L2-warm figure: the same graph back to back with no flush in between
+    # (the 256^3 tensors and intermediates partly stay in the 129 MB L2).
+    warm_steps = max(3, min(args.steps, 200))
+    wa, wb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(3):
+        ex.exsum_graph_launch(gexec, sh)
+    wa.record(stream)
+    for _ in range(warm_steps):
+        ex.exsum_graph_launch(gexec, sh)
+    wb.record(stream)
+    torch.cuda.synchronize()
+    warm_ms = wa.elapsed_time(wb) / warm_steps
     launches = launches_per_step * args.steps
     if world > 1:
         torch.distributed.barrier()
@@ -335,7 +349,8 @@ def run_ours(args):
         b = pass_bytes(name, level, elems, dtype)
         passes.append({"pos": pos, "kernel": name, "level": level, "elems": elems, "launches": cnt,
                        "mean_us": round(mean_ms * 1e3, 3), "share": 0.0,
-                       "algo_bytes": b, "achieved_gbs": round(b / (mean_ms * 1e-3) / 1e9, 1)})
+                       "algo_bytes": b, "achieved_gbs": round(b / (mean_ms * 1e-3) / 1e9, 1),
+                       "frac": round(b / (mean_ms * 1e-3) / 1e9 / peak, 4)})
     total_kernel_ms = sum(p["mean_us"] * p["launches"] for p in passes) or 1.0
     for p_ in passes:
         p_["share"] = round(p_["mean_us"] * p_["launches"] / total_kernel_ms, 4)
@@ -410,6 +425,22 @@ def run_ours(args):
         cpu, ref = cpu_baseline(vals, spec, budget_s=12.0)
         if ref is not None:
             accuracy = accuracy_vs_oracle(out.cpu().numpy(), ref, dtype, op)
+        try:
+            cpu["all_cores"] = cpu_all_cores(vals, spec, budget_s=6.0)
+        except Exception as e:  # no OpenMP-capable compiler on this host
+            cpu["all_cores"] = {"unavailable": str(e)[:200]}
+
+    # ---- compact batched and served figures (rank 0, N = 1) -----------------------------------
+    batched = served = None
+    if rank == 0 and world == 1 and not args.no_extras:
+        try:
+            batched = batched_bench(64, steps=10, warmup=2, plain_steps=2)
+        except Exception as e:
+            batched = {"error": str(e)[:300]}
+        try:
+            served = served_bench(1500)
+        except Exception as e:
+            served = {"error": str(e)[:300]}
 
     if rank == 0:
         line = {
@@ -425,7 +456,13 @@ def run_ours(args):
                                    round(one_rw / (ms_per_step * 1e-3) / 1e9, 1),
                                    "frac": round(one_rw / (ms_per_step * 1e-3) / 1e9 / peak, 4)},
             "passes": passes,
+            "lowest_level0_pass": (min((p_ for p_ in passes if p_["level"] == 0),
+                                       key=lambda p_: p_["frac"], default=None) or {}).get("kernel"),
+            "l2_warm": {"value": round(whole_job_rate(N, world, warm_ms * 1e-3) / 1e9, 3),
+                        "ms_per_step": round(warm_ms, 5), "steps": warm_steps,
+                        "note": "same graph back to back, no L2 flush between steps"},
             "e2e": e2e, "gpu_launches": launches, "clocks": clk, "cpu_baseline": cpu,
+            "batched": batched, "served": served,
             "accuracy": accuracy,
         }
         print(json.dumps(line), flush=True)
@@ -493,6 +530,29 @@ def cpu_baseline(vals, spec, budget_s):
                  rows, shape[0])}, None)
 
 
+def cpu_all_cores(vals, spec, budget_s):
+    """The same box-complement oracle with its independent rows spread over
+    all host cores (OpenMP variant, bit-identical results), on the whole
+    tensor."""
+    from oracle import oracle
+    shape, k, op = spec["shape"], spec["k"], spec["op"]
+    N = 1
+    for s_ in shape:
+        N *= s_
+    t0 = time.perf_counter()
+    oracle.box_complement_omp(vals, k, op)
+    first = time.perf_counter() - t0
+    runs = max(1, min(20, int(budget_s // max(first, 1e-6))))
+    t0 = time.perf_counter()
+    for _ in range(runs):
+        oracle.box_complement_omp(vals, k, op)
+    dt = time.perf_counter() - t0
+    return {"value": round(runs * N / dt / 1e9, 5), "unit": UNIT, "cores": oracle.omp_threads(),
+            "kind": "oracle_openmp", "nproc": os.cpu_count(),
+            "sample": "%d run(s) of the whole %s tensor, OpenMP oracle over rows" % (
+                runs, "x".join(map(str, shape)))}
+
+
 # ---- reference arm: the CPU oracle -------------------------------------------------------------
 
 def run_reference(args):
@@ -545,7 +605,9 @@ def run_reference(args):
 
 
 def run_profile_once(args):
-    """Two plain calls of the workload's excluded sum, for profilers."""
+    """Two plain calls of the workload's excluded sum, for profilers; the L2
+    is flushed (256 MiB written, then read back) before each call, as
+    between the bench's timed steps."""
     import numpy as np
     import torch
 
@@ -555,7 +617,10 @@ def run_profile_once(args):
     dev, _, spec = synth.workload_input(args.workload)
     x = (torch.from_numpy(np.ascontiguousarray(dev).view(np.int16)).view(torch.bfloat16)
          if spec["dtype"] == "bf16" else torch.from_numpy(np.ascontiguousarray(dev))).cuda()
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     for _ in range(2):
+        flush.fill_(1)
+        flush.view(torch.int64).max()
         ex.excluded(x, spec["k"], spec["op"])
     torch.cuda.synchronize()
     print(json.dumps({"profile_once": args.workload, "launches": ex.exsum_launch_count()}))
@@ -577,17 +642,18 @@ def _seeded_device_tensors(shapes, seed, dtype):
     return out
 
 
-def run_batched(args):
-    """512 uneven tensors: d in {2, 3}, sides uniform in [32, 512] (at most 2^24
-    elements), k_i uniform in [2, 32], fp32 uniform [-1, 1), +."""
+def batched_bench(count, seed=11, steps=20, warmup=3, plain_steps=3):
+    """`count` uneven tensors: d in {2, 3}, sides uniform in [32, 512] (at
+    most 2^24 elements), k_i uniform in [2, 32], fp32 uniform [-1, 1), +;
+    one planned, graph-captured batch against plain per-tensor launches on
+    one stream.  Returns the record."""
     import numpy as np
     import torch
 
     import paper_2106_00124_gb300 as ex
     from paper_2106_00124_gb300 import synth
-    torch.cuda.set_device(0)
-    spec = synth.batched_shapes(512, seed=11)
-    xs = _seeded_device_tensors([s_ for s_, _ in spec], 11, "f32")
+    spec = synth.batched_shapes(count, seed=seed)
+    xs = _seeded_device_tensors([s_ for s_, _ in spec], seed, "f32")
     outs = [torch.empty_like(x) for x in xs]
     descs = [ex.make_desc(x.data_ptr(), o.data_ptr(), sh, k, ex.OP_ADD, ex.F32)
              for x, o, (sh, k) in zip(xs, outs, spec)]
@@ -598,10 +664,9 @@ def run_batched(args):
     tune_s = time.perf_counter() - t0
     assert rc == 0, ex.strerror(rc)
     _, lanes, order, wsb, kernels = ex.exsum_batch_info(plan)
-    for _ in range(max(1, args.warmup)):
+    for _ in range(max(1, warmup)):
         ex.exsum_batch_launch(plan, stream.cuda_stream)
     torch.cuda.synchronize()
-    steps = max(3, min(args.steps, 20))
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record(stream)
     for _ in range(steps):
@@ -621,7 +686,6 @@ def run_batched(args):
     plain()
     torch.cuda.synchronize()
     ref = [o.clone() for o in outs[:8]]
-    plain_steps = 3
     a.record(stream)
     for _ in range(plain_steps):
         plain()
@@ -632,7 +696,7 @@ def run_batched(args):
     torch.cuda.synchronize()
     same = all(torch.equal(r_, o) for r_, o in zip(ref, outs[:8]))
     ex.exsum_batch_destroy(plan)
-    print(json.dumps({
+    return {
         "metric": "batched excluded-sum Gelem/s", "unit": "Gelem/s",
         "value": round(total / (batch_ms * 1e-3) / 1e9, 3),
         "plain_value": round(total / (plain_ms * 1e-3) / 1e9, 3),
@@ -642,53 +706,71 @@ def run_batched(args):
                      "kernels_per_launch": kernels, "lane_workspace_bytes": wsb,
                      "autotune_s": round(tune_s, 2)},
         "identical_to_plain": same, "dtype": "f32", "data": "synthetic (seeded, on device)",
-        "config": {"workload": "batched_512_uneven_d2d3_f32_add",
-                   "sides": [32, 512], "k": [2, 32], "cap": 1 << 24}}), flush=True)
+        "config": {"workload": "batched_%d_uneven_d2d3_f32_add" % count,
+                   "sides": [32, 512], "k": [2, 32], "cap": 1 << 24},
+        "plain": "the same tensors, one exsum_excluded_ws call each on one stream"}
 
 
-def run_served(args):
-    """A Poisson stream of excluded-sum requests (shapes and boxes as in the
-    batched workload, 90% fp32 +, 10% int64 max) served with continuous
-    batching at three offered loads, against one-at-a-time plain launches."""
+def run_batched(args):
+    """The 512-tensor batched workload."""
+    import torch
+    torch.cuda.set_device(0)
+    print(json.dumps(batched_bench(512, steps=max(3, min(args.steps, 20)), warmup=args.warmup)),
+          flush=True)
+
+
+def served_bench(nreq, slots=8, seed=12):
+    """A Poisson stream of `nreq` excluded-sum requests per offered load
+    (shapes and boxes as in the batched workload, 90% fp32 +, 10% int64 max)
+    served with continuous batching at 0.5, 0.8 and 1.0 of the saturated
+    rate, against plain launches: the same arrivals, each request one
+    exsum_excluded call on one stream as it arrives.  Returns the record."""
     import numpy as np
     import torch
 
     import paper_2106_00124_gb300 as ex
     from paper_2106_00124_gb300 import synth
-    torch.cuda.set_device(0)
-    f_spec = synth.batched_shapes(48, seed=12)
-    i_spec = synth.batched_shapes(8, seed=13)
-    fx = _seeded_device_tensors([s_ for s_, _ in f_spec], 12, "f32")
-    ix = _seeded_device_tensors([s_ for s_, _ in i_spec], 13, "i64")
+    f_spec = synth.batched_shapes(48, seed=seed)
+    i_spec = synth.batched_shapes(8, seed=seed + 1)
+    fx = _seeded_device_tensors([s_ for s_, _ in f_spec], seed, "f32")
+    ix = _seeded_device_tensors([s_ for s_, _ in i_spec], seed + 1, "i64")
     fo = [torch.empty_like(x) for x in fx]
     io = [torch.empty_like(x) for x in ix]
-    rng = np.random.default_rng(14)
-    nreq = args.requests
+    rng = np.random.default_rng(seed + 2)
     kinds = rng.random(nreq) < 0.1
     picks = [int(rng.integers(0, len(i_spec) if kd else len(f_spec))) for kd in kinds]
-    descs, sizes = [], []
+    descs, sizes, calls = [], [], []
     for kd, j in zip(kinds, picks):
         if kd:
             sh, k = i_spec[j]
-            descs.append(ex.make_desc(ix[j].data_ptr(), io[j].data_ptr(), sh, k, ex.OP_MAX, ex.I64))
+            args_ = (ix[j].data_ptr(), io[j].data_ptr(), len(sh), sh, k, ex.OP_MAX, ex.I64)
         else:
             sh, k = f_spec[j]
-            descs.append(ex.make_desc(fx[j].data_ptr(), fo[j].data_ptr(), sh, k, ex.OP_ADD, ex.F32))
+            args_ = (fx[j].data_ptr(), fo[j].data_ptr(), len(sh), sh, k, ex.OP_ADD, ex.F32)
+        descs.append(ex.make_desc(args_[0], args_[1], sh, k, args_[5], args_[6]))
+        calls.append(args_)
         sizes.append(int(np.prod(sh)))
     budget = 40 << 30
 
-    def serve(slots, rate, n):
+    def stats(lat, first, last, n):
+        span = (last - first) / 1e9
+        return {"p50_ms": round(float(np.percentile(lat, 50)), 3),
+                "p99_ms": round(float(np.percentile(lat, 99)), 3),
+                "throughput_req_s": round(n / span, 1),
+                "gelem_s": round(sum(sizes[:n]) / span / 1e9, 3)}
+
+    def arrivals_for(rate, n, start):
+        if rate is None:
+            return np.full(n, start, dtype=np.int64)
+        return (start + np.cumsum(rng.exponential(1e9 / rate, size=n))).astype(np.int64)
+
+    def serve(rate, n):
         srv = ex.exsum_server_create(budget, slots)
         assert srv
-        start = ex.exsum_server_now_ns() + 200_000_000
-        if rate is None:
-            arrivals = np.full(n, start, dtype=np.int64)
-        else:
-            gaps = rng.exponential(1e9 / rate, size=n)
-            arrivals = (start + np.cumsum(gaps)).astype(np.int64)
+        arr = arrivals_for(rate, n, ex.exsum_server_now_ns() + 200_000_000)
         tickets = []
         for i in range(n):
-            rc, t = ex.exsum_server_submit_at(srv, descs[i], 0, int(arrivals[i]))
+            rc, t = ex.exsum_server_submit_at(srv, descs[i], 0, int(arr[i]))
             assert rc == 0
             tickets.append(t)
         for t in tickets:
@@ -702,28 +784,56 @@ def run_served(args):
             first = sub if first is None else min(first, sub)
             last = max(last, done)
         ex.exsum_server_destroy(srv)
-        span = (last - first) / 1e9
-        el = sum(sizes[:n])
-        return {"p50_ms": round(float(np.percentile(lat, 50)), 3),
-                "p99_ms": round(float(np.percentile(lat, 99)), 3),
-                "throughput_req_s": round(n / span, 1), "gelem_s": round(el / span / 1e9, 3)}
+        return stats(lat, first, last, n)
 
-    slots = 8
-    sat = serve(slots, None, min(nreq, 4000))          # saturated: everything arrives at once
+    def plain(rate, n):
+        # one stream, one exsum_excluded call per request at its arrival
+        # time; completion times from events, mapped onto the host clock by
+        # a reference event recorded right before the first arrival
+        stream = torch.cuda.Stream()
+        sp = stream.cuda_stream
+        for c in calls[:8]:   # the stream's workspace and side streams exist before timing
+            ex.exsum_excluded(c[0], c[1], c[2], c[3], c[4], c[5], c[6], sp)
+        stream.synchronize()
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+        ref = torch.cuda.Event(enable_timing=True)
+        ref.record(stream)
+        stream.synchronize()
+        t_ref = ex.exsum_server_now_ns()
+        arr = arrivals_for(rate, n, t_ref + 50_000_000)
+        for i in range(n):
+            while ex.exsum_server_now_ns() < arr[i]:
+                pass
+            c = calls[i]
+            rc = ex.exsum_excluded(c[0], c[1], c[2], c[3], c[4], c[5], c[6], sp)
+            assert rc == 0, ex.strerror(rc)
+            evs[i].record(stream)
+        stream.synchronize()
+        done = [t_ref + int(ref.elapsed_time(e) * 1e6) for e in evs]
+        lat = [(d_ - a_) / 1e6 for d_, a_ in zip(done, arr)]
+        return stats(lat, int(arr[0]), max(done), n)
+
+    sat = serve(None, nreq)          # saturated: everything arrives at once
     sat_rate = sat["throughput_req_s"]
     loads = {}
     for f in (0.5, 0.8, 1.0):
         loads[str(f)] = {"offered_req_s": round(f * sat_rate, 1),
-                         "served": serve(slots, f * sat_rate, nreq),
-                         "plain": serve(1, f * sat_rate, nreq)}
-    print(json.dumps({
+                         "served": serve(f * sat_rate, nreq),
+                         "plain": plain(f * sat_rate, nreq)}
+    return {
         "metric": "served excluded-sum p50/p99 latency and throughput", "unit": "ms / req/s",
         "requests_per_load": nreq, "slots": slots, "budget_bytes": budget,
         "saturated": sat, "loads": loads, "dtype": "f32 (+ int64 max)",
         "data": "synthetic (seeded, on device)",
         "config": {"workload": "served_poisson_uneven_d2d3_f32add_i64max",
-                   "plain": "the same arrivals served one request at a time (1 slot)"}}),
-        flush=True)
+                   "plain": "the same arrivals, one exsum_excluded call each on one stream"}}
+
+
+def run_served(args):
+    """The served workload at its full request count."""
+    import torch
+    torch.cuda.set_device(0)
+    print(json.dumps(served_bench(args.requests)), flush=True)
 
 
 def main(argv=None):

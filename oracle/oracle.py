@@ -31,6 +31,9 @@ _LIB = os.path.join(_HERE, "libexsum_oracle.so")
 _MON = {("int", "add"): 0, ("int", "max"): 1, ("float", "add"): 2, ("float", "max"): 3}
 
 _lib = None
+_SRC_OMP = os.path.join(_HERE, "exsum_oracle_omp.c")
+_LIB_OMP = os.path.join(_HERE, "libexsum_oracle_omp.so")
+_lib_omp = None
 
 
 def build(force=False):
@@ -41,6 +44,35 @@ def build(force=False):
             ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
+
+
+def build_omp(force=False):
+    """Compiles the OpenMP variant of the box-complement oracle (the same
+    steps with independent rows spread over the host cores); without an
+    OpenMP-capable compiler it is built single-threaded."""
+    if force or not os.path.exists(_LIB_OMP) or os.path.getmtime(_LIB_OMP) < os.path.getmtime(_SRC_OMP):
+        tmp = _LIB_OMP + ".tmp%d" % os.getpid()
+        base = ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-o", tmp, _SRC_OMP, "-lm"]
+        try:
+            subprocess.check_call(base[:1] + ["-fopenmp"] + base[1:], stderr=subprocess.DEVNULL)
+        except subprocess.CalledProcessError:
+            subprocess.check_call(base)
+        os.replace(tmp, _LIB_OMP)
+    return _LIB_OMP
+
+
+def _load_omp():
+    global _lib_omp
+    if _lib_omp is None:
+        build_omp()
+        lib = ctypes.CDLL(_LIB_OMP)
+        p, i64p = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)
+        lib.orcp_box_complement.argtypes = [p, p, ctypes.c_int, i64p, i64p, ctypes.c_int]
+        lib.orcp_box_complement.restype = ctypes.c_int
+        lib.orcp_threads.argtypes = []
+        lib.orcp_threads.restype = ctypes.c_int
+        _lib_omp = lib
+    return _lib_omp
 
 
 def _load():
@@ -116,6 +148,24 @@ def bdbs(a, k, op):
 def box_complement(a, k, op):
     """Excluded sums by the box-complement algorithm (Sec. 5)."""
     return _call_full("orc_box_complement", a, k, op)
+
+
+def box_complement_omp(a, k, op):
+    """box_complement with independent rows on all host cores (OpenMP);
+    the same steps and operand order, so the same bits."""
+    lib = _load_omp()
+    w = _widen(a)
+    out = np.empty_like(w)
+    mon = _MON[(_kind(a), op)]
+    rc = lib.orcp_box_complement(w.ctypes.data, out.ctypes.data, w.ndim, _i64(w.shape), _i64(k), mon)
+    if rc != 0:
+        raise ValueError("orcp_box_complement failed with status %d" % rc)
+    return out
+
+
+def omp_threads():
+    """Host threads the OpenMP oracle uses (1 if built without OpenMP)."""
+    return int(_load_omp().orcp_threads())
 
 
 def corners(a, k, op):
