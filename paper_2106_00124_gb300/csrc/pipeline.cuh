@@ -16,6 +16,7 @@
 
 #include "kernels_flat.cuh"
 #include "kernels_fold.cuh"
+#include "kernels_line1d.cuh"
 #include "kernels_rowbulk.cuh"
 #include "kernels_rows.cuh"
 
@@ -248,6 +249,7 @@ struct Pipe {
 
     // ---- dimension-1 step: prefix/suffix along dim 1 + contributions --------------------
     static constexpr int CT_NT = 256, CT_V = 16, CT_L = CT_NT * CT_V;  // contiguous segment
+    static constexpr int LN_NT = 256, LN_V = 16, LN_L = LN_NT * LN_V;  // one long line, 16-byte path
 
     template <class SH, class SOut>
     static void exline_stage(Ctx &cx, const SH *H, const CAR *T, SOut *out, int64_t n1,
@@ -255,7 +257,10 @@ struct Pipe {
     {
         if (!cx.ok()) return;
         const bool contig = (Mc == 1);
-        const int64_t L = contig ? CT_L : EXL;
+        // one long line with a 4-byte local type: 16-byte loads and stores
+        // (kernels_line1d.cuh)
+        const bool line = contig && sizeof(L_) == 4 && T == nullptr;
+        const int64_t L = line ? LN_L : (contig ? CT_L : EXL);
         const int64_t S = cdiv(n1, L);
         const CAR *Q = T;
         int64_t qs = 0;
@@ -266,34 +271,50 @@ struct Pipe {
             const bool blk = S > 64 && Mc < 4096;
             CAR *SR = blk ? cx.take<CAR>(S * Mc) : nullptr;
             if (cx.dry || !cx.ok()) return;
-            cx.before(TAG_REDUCE, n1 * Mc);
-            if (contig)
-                k_reduce_seg_contig<M, SH, CT_NT, CT_V><<<(unsigned)S, CT_NT, 0, cx.stream>>>(
-                    H, R, Rt, n1, k1 % L);
-            else
-                k_reduce_seg2<M, SH><<<(unsigned)cdiv(S * Mc, 256), 256, 0, cx.stream>>>(
-                    H, R, Rt, n1, Mc, L, S, k1 % L);
-            cx.check_launch();
             const int64_t qoff = 1 + k1 / L;
-            cx.before(TAG_CARRY, S * Mc);
-            if (blk)
-                k_carry_blk<M, 1024><<<(unsigned)Mc, 1024, 0, cx.stream>>>(R, Rt, T, Qb, SR, Mc, S,
-                                                                           qoff, nullptr);
-            else
-                k_carry_col<M><<<(unsigned)cdiv(Mc, 256), 256, 0, cx.stream>>>(R, Rt, T, Qb, Mc, S,
-                                                                                qoff);
-            cx.check_launch();
+            if (line) {
+                const int vec = ((((uintptr_t)H) & (sizeof(SH) * 4 - 1)) == 0) ? 1 : 0;
+                cx.before(TAG_REDUCE, n1);
+                k_reduce_line<M, SH, LN_NT, LN_V><<<(unsigned)S, LN_NT, 0, cx.stream>>>(H, R, Rt, n1, k1 % L, vec);
+                cx.check_launch();
+                cx.before(TAG_CARRY, S);
+                k_carry_line2<M, 1024><<<(unsigned)cdiv(S, 1024), 1024, 0, cx.stream>>>(R, Rt, Qb, S, qoff);
+                cx.check_launch();
+            } else {
+                cx.before(TAG_REDUCE, n1 * Mc);
+                if (contig)
+                    k_reduce_seg_contig<M, SH, CT_NT, CT_V><<<(unsigned)S, CT_NT, 0, cx.stream>>>(
+                        H, R, Rt, n1, k1 % L);
+                else
+                    k_reduce_seg2<M, SH><<<(unsigned)cdiv(S * Mc, 256), 256, 0, cx.stream>>>(
+                        H, R, Rt, n1, Mc, L, S, k1 % L);
+                cx.check_launch();
+                cx.before(TAG_CARRY, S * Mc);
+                if (blk)
+                    k_carry_blk<M, 1024><<<(unsigned)Mc, 1024, 0, cx.stream>>>(R, Rt, T, Qb, SR, Mc, S,
+                                                                               qoff, nullptr);
+                else
+                    k_carry_col<M><<<(unsigned)cdiv(Mc, 256), 256, 0, cx.stream>>>(R, Rt, T, Qb, Mc, S,
+                                                                                    qoff);
+                cx.check_launch();
+            }
             Q = Qb;
             qs = Mc;
         }
         if (cx.dry || !cx.ok()) return;
         cx.before(TAG_EXLINE, n1 * Mc);
-        if (contig)
+        if (line) {
+            const int vin = ((((uintptr_t)H) & (sizeof(SH) * 4 - 1)) == 0) ? 1 : 0;
+            const int vout = ((((uintptr_t)out) & 15) == 0 && sizeof(SOut) == 4) ? 1 : 0;
+            k_exline_line<M, SH, SOut, LN_NT, LN_V><<<(unsigned)S, LN_NT, 0, cx.stream>>>(
+                H, Q, out, n1, k1, vin, vin && (k1 % 4) == 0 ? 1 : 0, vout);
+        } else if (contig) {
             k_exline_contig<M, SH, SOut, CT_NT, CT_V><<<(unsigned)S, CT_NT, 0, cx.stream>>>(
                 H, Q, out, n1, k1);
-        else
+        } else {
             k_exline2<M, SH, SOut, EXL><<<(unsigned)cdiv(S * Mc, 128), 128, 0, cx.stream>>>(
                 H, Q, qs, nullptr, out, n1, Mc, k1, S);
+        }
         cx.check_launch();
     }
 
