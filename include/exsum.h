@@ -163,7 +163,11 @@ int exsum_excluded_ws(const void *in, void *out, int d, const int64_t *shape, co
  *     (keep the launch trace off, its default, when calling it).
  *   - The first call on a device looks up the device address of the buffer
  *     (cudaGetSymbolAddress, with that device current); make that first
- *     call before any stream capture on that device.
+ *     call before any stream capture on that device.  Later calls made
+ *     outside a capture look it up again (cheap), so a cudaDeviceReset
+ *     between calls is safe; calls inside a capture use the address of the
+ *     last uncaptured call, so do not reset the device between that call
+ *     and the capture.
  *   - All calls on a device share the one buffer, and a call leaves its
  *     intermediates there; the pipeline writes every scratch word before it
  *     reads it, so nothing needs clearing between calls.  Calls whose work
@@ -325,6 +329,11 @@ const char *exsum_kernel_name(int tag);
 
 /* Kernels launched by the library in this process so far. */
 int64_t exsum_launch_count(void);
+
+/* Side streams the library has created in this process so far (two per
+ * caller stream on which an excluded sum first forked; diagnostics, no
+ * counterpart in the paper). */
+int64_t exsum_side_streams_created(void);
 
 /*
  * Graph helpers (no counterpart in the paper).  Calls captured into a CUDA

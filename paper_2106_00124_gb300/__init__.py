@@ -94,6 +94,7 @@ _SIG = {
                              ctypes.c_int, ctypes.c_int], ctypes.c_int),
     "exsum_kernel_name": ([ctypes.c_int], ctypes.c_char_p),
     "exsum_launch_count": ([], ctypes.c_int64),
+    "exsum_side_streams_created": ([], ctypes.c_int64),
     "exsum_excluded_weak": ([_P, _P, ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
                              ctypes.POINTER(ctypes.c_int64), ctypes.c_int, _P], ctypes.c_int),
     "exsum_graph_instantiate": ([_P, ctypes.POINTER(_P)], ctypes.c_int),
@@ -243,6 +244,10 @@ def exsum_kernel_name(tag):
 
 def exsum_launch_count():
     return int(_load().exsum_launch_count())
+
+
+def exsum_side_streams_created():
+    return int(_load().exsum_side_streams_created())
 
 
 def exsum_graph_instantiate(graph):

@@ -32,6 +32,7 @@ struct TraceRec {
     cudaEvent_t ev0, ev1;
 };
 std::atomic<int64_t> g_launches{0};
+std::atomic<int64_t> g_side_streams{0};
 std::atomic<int> g_trace_on{0};
 std::mutex g_trace_mu;
 std::vector<TraceRec> g_trace;
@@ -147,6 +148,7 @@ static const exsum::Aux *aux_for(void *stream)
         cudaGetLastError();
         a = exsum::Aux();
     }
+    if (a.side) g_side_streams.fetch_add(2);
     g_aux[key] = a;
     return a.side ? &g_aux[key] : nullptr;
 }
@@ -475,6 +477,8 @@ const char *exsum_kernel_name(int tag)
 }
 
 int64_t exsum_launch_count(void) { return g_launches.load(); }
+
+int64_t exsum_side_streams_created(void) { return g_side_streams.load(); }
 
 int exsum_graph_instantiate(void *graph, void **exec)
 {

@@ -15,8 +15,9 @@
 // The array's name, used in host code, is only a host-side stand-in for the
 // device variable; passing it to a kernel would fault or (where the GPU can
 // reach host memory) silently use the wrong memory.  The device address is
-// therefore looked up with cudaGetSymbolAddress once per device, with that
-// device current, on the first call made on that device.
+// therefore looked up with cudaGetSymbolAddress, with the device current, on
+// the first call made on that device and again on every later call made
+// outside a stream capture (a device reset moves it).
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -48,10 +49,19 @@ extern "C" int exsum_excluded_noalloc(const void *in, void *out, int d, const in
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) return EXSUM_ECUDA;
+    // The address is looked up again on every call made outside a stream
+    // capture, so that a device reset (which reloads the library's device
+    // image at a new address) never leaves a stale pointer behind; inside a
+    // capture the address from the last uncaptured call is used.
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing((cudaStream_t)stream, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return EXSUM_ECUDA;
+    }
     void *scratch = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_noalloc_mu);
-        if (!g_noalloc_ptr[dev]) {
+        if (cs == cudaStreamCaptureStatusNone || !g_noalloc_ptr[dev]) {
             void *p = nullptr;
             e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
             if (e != cudaSuccess || !p) {

@@ -15,6 +15,8 @@
 //                   and H1 the window of k1 planes of R -- the row schedule
 //                   once more, one block per x1 (Sec. 4, Theorem "Recursive
 //                   Box-complement", the last dimension peeled).
+// The same two kernels are a whole excluded sum of a small d = 2 tensor
+// (read as R, written as T, in the compensated accumulator throughout).
 // Every reduction runs in a fixed order, so results do not depend on timing.
 #pragma once
 
@@ -117,9 +119,16 @@ k_inc_strided4_rt(const SIn *__restrict__ in, SOut *__restrict__ out, int n, int
     __syncwarp();
     const int x = r0 + lane;
     if (x < rend) {
-        Lt t = acc[lane][0];
+        // pairwise (tree) combination of the 32 lanes' values, in a fixed
+        // order: rounding grows with the tree depth, not the count
+        Lt w[32];
 #pragma unroll
-        for (int c = 1; c < 32; ++c) t = M::lop(t, acc[lane][c]);
+        for (int c = 0; c < 32; ++c) w[c] = acc[lane][c];
+#pragma unroll
+        for (int h = 16; h >= 1; h >>= 1)
+#pragma unroll
+            for (int c = 0; c < h; ++c) w[c] = M::lop(w[c], w[c + h]);
+        const Lt t = w[0];
         const int64_t p0 = 4 * (i4 - lane);   // first inner position of the warp
         const int64_t rows_per_x1 = I / L;
         const int H = L >> 7;
@@ -194,10 +203,10 @@ k_plane_totals(const SP *__restrict__ P, int H, typename M::car_t *__restrict__ 
 // totals are scanned across the block (warp shuffles, then the warp totals),
 // in both directions.
 // ---------------------------------------------------------------------------
-template <class M>
+template <class M, class SR = typename M::car_t, class ST = typename M::car_t>
 __global__ void __launch_bounds__(256)
-k_exc2d(const typename M::car_t *__restrict__ R, const typename M::car_t *__restrict__ R2,
-        typename M::car_t *__restrict__ T, int n1, int n2, int k1, int k2)
+k_exc2d(const SR *__restrict__ R, const typename M::car_t *__restrict__ R2, ST *__restrict__ T, int n1,
+        int n2, int k1, int k2)
 {
     using A = typename M::acc_t;
     using C = typename M::car_t;
@@ -229,11 +238,11 @@ k_exc2d(const typename M::car_t *__restrict__ R, const typename M::car_t *__rest
     // window of k1 planes
     const int kw = min(k1, n1 - x1);
     for (int x2 = tid; x2 < n2; x2 += nt) {
-        const C *col = R + (int64_t)x1 * n2 + x2;
+        const SR *col = R + (int64_t)x1 * n2 + x2;
         A h = M::get(col[0]);
         // eight loads in flight per round
         for (int i0 = 1; i0 < kw; i0 += 8) {
-            C v[8];
+            SR v[8];
 #pragma unroll
             for (int i = 0; i < 8; ++i)
                 if (i0 + i < kw) v[i] = col[(int64_t)(i0 + i) * n2];
@@ -284,7 +293,7 @@ k_exc2d(const typename M::car_t *__restrict__ R, const typename M::car_t *__rest
     __syncthreads();
     for (int x2 = tid; x2 < n2; x2 += nt) {
         const A s = x2 + k2 < n2 ? sf[x2 + k2] : M::id();
-        T[(int64_t)x1 * n2 + x2] = M::template put<C>(M::op(t2, M::op(hv[x2], s)));
+        T[(int64_t)x1 * n2 + x2] = M::template put<ST>(M::op(t2, M::op(hv[x2], s)));
     }
 }
 

@@ -328,8 +328,12 @@ k_rowx_bulk(const typename M::loc_t *__restrict__ in, const typename M::car_t *_
         for (int i = tid; i < (RSA - (TR + halo)) * L; i += NT) stage0[(b * RSA + TR + halo) * L + i] = M::lid();
 
     // Column groups and row segments of the walk, fixed for the kernel.
+    // (aligned walk: the planner's segments of whole k2-blocks; generic
+    // walk: segments of at least 2 k2 rows, so that a segment's look-ahead
+    // does not dominate what it reads)
     const int LQ = L / CW;
-    const int G = LQ >= NT ? 1 : NT / LQ;
+    int G = LQ >= NT ? 1 : NT / LQ;
+    if (!al && k2 > 1) G = max(1, min(G, TR / (2 * k2)));
     const int SL = (TR + G - 1) / G;
     constexpr int NP = 4 / CW;   // (column group, segment) pairs per thread for L <= 1024, NT >= 256
     int pc[NP], ps[NP];
@@ -514,6 +518,8 @@ k_rowx_bulk(const typename M::loc_t *__restrict__ in, const typename M::car_t *_
                 }
             }
             __syncwarp();
+            // results over the strip, in place -- never into the padding
+            // columns [L, LP), which must keep the identity for later tiles
 #pragma unroll
             for (int i = 0; i < EPL / 4; ++i) {
                 SOut o4[4];
@@ -521,7 +527,7 @@ k_rowx_bulk(const typename M::loc_t *__restrict__ in, const typename M::car_t *_
                 for (int m = 0; m < 4; ++m) o4[m] = finish<M, SOut>(tv, res[4 * i + m]);
                 uint4 w;
                 memcpy(&w, o4, 16);
-                *reinterpret_cast<uint4 *>(row + toff[i]) = w;
+                if (LP == L || e0 + 4 * i < L) *reinterpret_cast<uint4 *>(row + toff[i]) = w;
             }
             __syncwarp();
             // coalesced copy-out of this warp's rows

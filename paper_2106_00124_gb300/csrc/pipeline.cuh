@@ -502,31 +502,38 @@ struct Pipe {
 
     // Geometry of k_rowx_bulk for rows of L elements, a window of kk rows
     // along n2 (1: none; kmax its compile-time bound) and O2 slices of n2
-    // rows.  Strips of 32 elements (16 for L <= 128); NT = 256 threads with
-    // two staging buffers; the tallest tile (at most 64 rows, a multiple of
-    // the rows one row pass covers and of the walk's segments) that lets
-    // two blocks share an SM, else one.  EXSUM_ROWX_TR, EXSUM_ROWX_NBUF,
-    // EXSUM_ROWX_EPL and EXSUM_ROWX_NT override (tuning).
+    // rows: strips of 32 elements, 256 threads; two staging buffers and the
+    // tallest tile (at most 64 rows, a multiple of the rows one row pass
+    // covers and of the walk's segments) that lets two blocks share an SM,
+    // else one staging buffer, else one block per SM.  EXSUM_ROWX_TR and
+    // EXSUM_ROWX_NBUF override (tuning).
     static BulkPlan bulk_plan(int64_t L, int64_t n2, int64_t O2, int kk, int kmax, int64_t sms)
     {
         BulkPlan bp;
+        // (shorter rows stay with k_rowx: tiles of a few KB and walks over a
+        // handful of columns cost more than the bulk copies save)
         if (sizeof(L_) != 4 || (L & 3) || L < 128 || L > 1024 || kk > 32) return bp;
-        int epl = env_int("EXSUM_ROWX_EPL", 0);
-        if (epl != 16 && epl != 32) epl = L <= 128 ? 16 : 32;
-        int lpr = 32;
-        while (lpr > 4 && (int64_t)(lpr / 2) * epl >= L) lpr >>= 1;
-        if ((int64_t)lpr * epl < L) return bp;
+        // strips of 32 elements, 4 .. 32 lanes per row
+        const int epl = 32;
+        int lpr = 4;
+        while (lpr < 32 && (int64_t)lpr * epl < L) lpr <<= 1;
         const int LP = lpr * epl;
         const int LSW = (LP + 31) & ~31;
         const int nt = 256;
         const int nb_env = env_int("EXSUM_ROWX_NBUF", 0);
         const int rows_pass = (nt / 32) * (32 / lpr);
         const int G = rowbulk_segs((int)L, kmax, nt);
+        // block-aligned walk when the tile can be a multiple of the segments
+        // times the window (at most 64 rows), else the generic walk
+        bool kfull = kk > 1 && kk == kmax;
         int step = rows_pass;
-        while (step % G) step += rows_pass;
-        const bool kfull = kk > 1 && kk == kmax;
-        if (kfull)
-            while ((step / G) % kk) step += rows_pass;
+        if (kfull) {
+            while (step <= 64 && (step % G || (step / G) % kk)) step += rows_pass;
+            if (step > 64) {
+                kfull = false;
+                step = rows_pass;
+            }
+        }
         const int tr_env = env_int("EXSUM_ROWX_TR", 0);
         auto sm = [&](int tr, int nb) {
             const bool al = kfull && (tr / G) % kk == 0 && tr % G == 0;
@@ -536,6 +543,7 @@ struct Pipe {
         // candidates in order of preference: (staging buffers, blocks per SM)
         const int cand[3][2] = {{2, 2}, {1, 2}, {1, 1}};
         int TR = 0, nbuf = 1, bps = 2;
+        const int trmax = step > 64 ? step : 64;
         for (int c = 0; c < 3 && !TR; ++c) {
             const int nb = cand[c][0];
             if (nb_env && nb != nb_env) continue;
@@ -544,7 +552,7 @@ struct Pipe {
                 const int tr = (tr_env + step - 1) / step * step;
                 if (sm(tr, nb) <= lim) TR = tr;
             } else {
-                for (int tr = (64 / step) * step; tr >= step && !TR; tr -= step)
+                for (int tr = (trmax / step) * step; tr >= step && !TR; tr -= step)
                     if (sm(tr, nb) <= lim) TR = tr;
             }
             if (TR) {
@@ -593,31 +601,29 @@ struct Pipe {
     {
         // row lengths fixed at compile time for the common block-aligned cases
         if constexpr (KM == 4 || KM == 8) {
-            if (bp.nt == 256 && bp.aligned && bp.LSW == L && bp.lpr * bp.epl == L) {
-                if (L == 256 && bp.epl == 32) {
+            if (bp.aligned && bp.LSW == L && bp.lpr * bp.epl == L) {
+                if (L == 256) {
                     if (bp.nbuf == 2)
                         rowbulk_go<SOut, KM, 32, 2, 256, 256>(cx, bp, src, T, out, n2, L, kk, k3);
                     else
                         rowbulk_go<SOut, KM, 32, 1, 256, 256>(cx, bp, src, T, out, n2, L, kk, k3);
                     return;
                 }
-                if (L == 512 && bp.epl == 32) {
+                if (L == 512) {
                     if (bp.nbuf == 2)
                         rowbulk_go<SOut, KM, 32, 2, 256, 512>(cx, bp, src, T, out, n2, L, kk, k3);
                     else
                         rowbulk_go<SOut, KM, 32, 1, 256, 512>(cx, bp, src, T, out, n2, L, kk, k3);
                     return;
                 }
-                if (L == 128 && bp.epl == 16 && bp.nbuf == 2) {
-                    rowbulk_go<SOut, KM, 16, 2, 256, 128>(cx, bp, src, T, out, n2, L, kk, k3);
+                if (L == 128 && bp.nbuf == 2) {
+                    rowbulk_go<SOut, KM, 32, 2, 256, 128>(cx, bp, src, T, out, n2, L, kk, k3);
                     return;
                 }
             }
         }
         if (bp.nbuf == 1)
             rowbulk_go<SOut, KM, 32, 1, 256>(cx, bp, src, T, out, n2, L, kk, k3);
-        else if (bp.epl == 16)
-            rowbulk_go<SOut, KM, 16, 2, 256>(cx, bp, src, T, out, n2, L, kk, k3);
         else
             rowbulk_go<SOut, KM, 32, 2, 256>(cx, bp, src, T, out, n2, L, kk, k3);
     }
@@ -636,7 +642,7 @@ struct Pipe {
             BulkPlan bp = bulk_plan(L, n2, O2, kk, kmax, cx.sms);
             if (!bp.ok) return false;
             bp.pdl = pdl;
-            if (bp.nt != 256 || (bp.nbuf == 1 && bp.epl != 32)) return false;
+            if (bp.nt != 256 || bp.epl != 32) return false;
             if (kmax == 1)
                 rowbulk_epl<SOut, 1>(cx, bp, src, T, out, n2, L, 1, k3);
             else if (kmax == 4)
@@ -874,6 +880,25 @@ struct Pipe {
         const int64_t M1 = N / n[0];
         if (d == 1) {
             exline_stage<SIn, SOut>(cx, X, nullptr, out, n[0], 1, k[0]);
+            return;
+        }
+        // A small two-dimensional tensor: plane totals, then one block per
+        // row of the output (kernels_fold.cuh), the whole sum in the long
+        // accumulator -- two short kernels instead of a chain of passes.
+        if (d == 2 && n[1] <= 4096 && k[0] <= 64 && N <= (1 << 20) && k[0] * N <= (1 << 24) &&
+            env_int("EXSUM_SMALL2D", 1) != 0) {
+            CAR *R2 = cx.take<CAR>(n[0]);
+            if (cx.dry || !cx.ok()) return;
+            cx.before(TAG_PLANE, N);
+            k_plane_totals<MC, SIn><<<(unsigned)n[0], 256, 0, cx.stream>>>(X, 1, nullptr, R2, (int)n[1]);
+            cx.check_launch();
+            const size_t smem = 2 * (size_t)n[1] * sizeof(typename MC::acc_t);
+            auto kern = k_exc2d<MC, SIn, SOut>;
+            if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cx.before(TAG_EXC2D, N);
+            launch_pdl(kern, (unsigned)n[0], 256, smem, cx.stream, X, (const CAR *)R2, out, (int)n[0], (int)n[1],
+                       (int)k[0], (int)k[1]);
+            cx.check_launch();
             return;
         }
         const RowPlan rp = row_plan(d, n, k, cx.sms);

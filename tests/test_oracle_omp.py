@@ -3,6 +3,8 @@ all-core CPU baseline) gives the single-threaded oracle's results bit for
 bit: it performs the same steps with the same operand order, only on
 several host threads.  CPU only."""
 
+import zlib
+
 import numpy as np
 import pytest
 
@@ -23,7 +25,7 @@ CASES = [
 
 @pytest.mark.parametrize("shape,k,op,kind", CASES)
 def test_omp_oracle_equals_single_threaded(shape, k, op, kind):
-    rng = np.random.default_rng(abs(hash((shape, k, op, kind))) % (1 << 31))
+    rng = np.random.default_rng(zlib.crc32(repr((shape, k, op, kind)).encode()))
     a = rng.uniform(-1, 1, shape) if kind == "float" else rng.integers(-1000, 1000, shape)
     ref = O.box_complement(a, k, op)
     got = O.box_complement_omp(a, k, op)

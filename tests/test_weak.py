@@ -2,6 +2,8 @@
 included, integer + only.  Checked against the oracle's BDBSC and against the
 strong excluded sum, which it equals exactly for wrapping integer +."""
 
+import zlib
+
 import numpy as np
 import pytest
 
@@ -25,7 +27,7 @@ def test_weak_rejects_float_and_bad_args():
 @pytest.mark.parametrize("shape,k", CASES, ids=[str(c[0]) + "k" + str(c[1]) for c in CASES])
 def test_weak_equals_oracle_and_strong(shape, k, dtype):
     import torch
-    dev, vals = seeded(shape, dtype, hash((shape, k, dtype)) & 0xFFFF, "add")
+    dev, vals = seeded(shape, dtype, zlib.crc32(repr((shape, k, dtype)).encode()) & 0xFFFF, "add")
     x = to_device(dev, dtype)
     weak = ex.excluded_weak(x, k)
     strong = ex.excluded(x, k, "add")

@@ -59,3 +59,31 @@ def test_noalloc_rejects_oversize_without_work():
     rc = ex.exsum_excluded_noalloc(x.data_ptr(), x.data_ptr() + 16, 3, shape, k, ex.OP_ADD,
                                    ex.F32, 0)
     assert rc == ex.EXSUM_ENOMEM
+
+
+def test_noalloc_allocates_nothing_and_forks_nothing():
+    """The promise itself: with the library's cached workspaces released and
+    the launch trace off, calls on a stream the library has never seen leave
+    the device's free memory and the library's side-stream count unchanged
+    (the first call on the device, which loads the library image holding the
+    static buffer, is made before measuring)."""
+    import torch
+    shape, k, dtype, op = CASES[0]
+    dev, _ = seeded(shape, dtype, 98, op)
+    x = to_device(dev, dtype)
+    _noalloc(x, shape, k, op, dtype)          # first call on this device
+    assert ex.exsum_release_cached_workspace() == ex.EXSUM_OK
+    ex.exsum_trace_enable(False)
+    s = torch.cuda.Stream()
+    out = torch.empty(shape, dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    streams0 = ex.exsum_side_streams_created()
+    for _ in range(2):
+        rc = ex.exsum_excluded_noalloc(x.data_ptr(), out.data_ptr(), len(shape), shape, k,
+                                       ex.OPS[op], ex.DTYPES[dtype], s.cuda_stream)
+        assert rc == ex.EXSUM_OK, ex.strerror(rc)
+    s.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert ex.exsum_side_streams_created() == streams0
