@@ -51,12 +51,11 @@ __device__ __forceinline__ void bdbs_walk(int k, int r0, int rend, LD ld, ST st)
 // consecutive inner positions, so every load and store is coalesced.
 // ---------------------------------------------------------------------------
 template <class M, class SIn, class SOut, int KMAX>
-__global__ void __launch_bounds__(128)
-k_inc_strided(const SIn *__restrict__ in, SOut *__restrict__ out, int64_t O, int n, int64_t I,
-              int k, int Lc, int nchunks)
+__device__ __forceinline__ void k_inc_strided_body(const SIn *__restrict__ in, SOut *__restrict__ out, int64_t O, int n, int64_t I,
+              int k, int Lc, int nchunks, int64_t vbid, int64_t vgrid)
 {
     const int64_t total = O * nchunks * I;
-    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t gid = (int64_t)vbid * blockDim.x + threadIdx.x;
     if (gid >= total) return;
     const int64_t i = gid % I;
     const int64_t rest = gid / I;
@@ -74,6 +73,14 @@ k_inc_strided(const SIn *__restrict__ in, SOut *__restrict__ out, int64_t O, int
         [&](int x, typename M::loc_t v) {
             st_hint(dst + (int64_t)x * I, M::template lput<SOut>(v), pol_out);
         });
+}
+
+template <class M, class SIn, class SOut, int KMAX>
+__global__ void __launch_bounds__(128)
+k_inc_strided(const SIn *__restrict__ in, SOut *__restrict__ out, int64_t O, int n, int64_t I,
+              int k, int Lc, int nchunks)
+{
+    k_inc_strided_body<M, SIn, SOut, KMAX>(in, out, O, n, I, k, Lc, nchunks, blockIdx.x, gridDim.x);
 }
 
 // ---------------------------------------------------------------------------

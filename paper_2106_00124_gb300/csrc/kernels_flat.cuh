@@ -72,14 +72,13 @@ __device__ __forceinline__ void store4(SOut *p, bool vec, int valid, const typen
 // stores -- the register BDBS walk of bdbs_walk on four columns.
 // ---------------------------------------------------------------------------
 template <class M, class SIn, class SOut, int KMAX>
-__global__ void __launch_bounds__(128)
-k_inc_strided4(const SIn *__restrict__ in, SOut *__restrict__ out, int64_t O, int n, int64_t I,
-               int k, int Lc, int nchunks)
+__device__ __forceinline__ void k_inc_strided4_body(const SIn *__restrict__ in, SOut *__restrict__ out, int64_t O, int n, int64_t I,
+               int k, int Lc, int nchunks, int64_t vbid, int64_t vgrid)
 {
     using Lt = typename M::loc_t;
     const int64_t I4 = I >> 2;
     const int64_t total = O * nchunks * I4;
-    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t gid = (int64_t)vbid * blockDim.x + threadIdx.x;
     if (gid >= total) return;
     const int64_t i4 = gid % I4;
     const int64_t rest = gid / I4;
@@ -139,6 +138,14 @@ k_inc_strided4(const SIn *__restrict__ in, SOut *__restrict__ out, int64_t O, in
 #pragma unroll
             for (int c = 0; c < 4; ++c) S[j][c] = M::lop(v[j][c], S[j + 1][c]);
     }
+}
+
+template <class M, class SIn, class SOut, int KMAX>
+__global__ void __launch_bounds__(128)
+k_inc_strided4(const SIn *__restrict__ in, SOut *__restrict__ out, int64_t O, int n, int64_t I,
+               int k, int Lc, int nchunks)
+{
+    k_inc_strided4_body<M, SIn, SOut, KMAX>(in, out, O, n, I, k, Lc, nchunks, blockIdx.x, gridDim.x);
 }
 
 __device__ __forceinline__ void cp_async_wait_all()

@@ -163,14 +163,13 @@ __device__ __forceinline__ typename M::acc_t block_reduce(typename M::acc_t v, t
 // (R[x1, x2], written unless R is null) and their total over x2 (R2[x1]).
 // ---------------------------------------------------------------------------
 template <class M, class SP>
-__global__ void __launch_bounds__(256)
-k_plane_totals(const SP *__restrict__ P, int H, typename M::car_t *__restrict__ R,
-               typename M::car_t *__restrict__ R2, int n2)
+__device__ __forceinline__ void k_plane_totals_body(const SP *__restrict__ P, int H, typename M::car_t *__restrict__ R,
+               typename M::car_t *__restrict__ R2, int n2, int64_t vbid, int64_t vgrid)
 {
     using A = typename M::acc_t;
     using C = typename M::car_t;
     __shared__ A red[33];
-    const int64_t x1 = blockIdx.x;
+    const int64_t x1 = vbid;
     pdl_trigger();
     pdl_wait();   // P comes from the kernel before
     A tot = M::id();
@@ -192,6 +191,14 @@ k_plane_totals(const SP *__restrict__ P, int H, typename M::car_t *__restrict__ 
     if (threadIdx.x == 0) R2[x1] = M::template put<C>(tot);
 }
 
+template <class M, class SP>
+__global__ void __launch_bounds__(256)
+k_plane_totals(const SP *__restrict__ P, int H, typename M::car_t *__restrict__ R,
+               typename M::car_t *__restrict__ R2, int n2)
+{
+    k_plane_totals_body<M, SP>(P, H, R, R2, n2, blockIdx.x, gridDim.x);
+}
+
 // ---------------------------------------------------------------------------
 // Excluded sums of the n1 x n2 tensor R with box (k1, k2), given its plane
 // totals R2 (one block per x1, k1 <= 64, n2 <= 4096; dynamic shared memory
@@ -204,9 +211,8 @@ k_plane_totals(const SP *__restrict__ P, int H, typename M::car_t *__restrict__ 
 // in both directions.
 // ---------------------------------------------------------------------------
 template <class M, class SR = typename M::car_t, class ST = typename M::car_t>
-__global__ void __launch_bounds__(256)
-k_exc2d(const SR *__restrict__ R, const typename M::car_t *__restrict__ R2, ST *__restrict__ T, int n1,
-        int n2, int k1, int k2)
+__device__ __forceinline__ void k_exc2d_body(const SR *__restrict__ R, const typename M::car_t *__restrict__ R2, ST *__restrict__ T, int n1,
+        int n2, int k1, int k2, int64_t vbid, int64_t vgrid)
 {
     using A = typename M::acc_t;
     using C = typename M::car_t;
@@ -216,7 +222,7 @@ k_exc2d(const SR *__restrict__ R, const typename M::car_t *__restrict__ R2, ST *
     __shared__ A red[33];
     __shared__ A wpre[32], wsuf[32];
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
-    const int x1 = blockIdx.x;
+    const int x1 = vbid;
     pdl_trigger();
     pdl_wait();   // R and R2 come from the kernel before
     // the one-dimensional part
@@ -295,6 +301,14 @@ k_exc2d(const SR *__restrict__ R, const typename M::car_t *__restrict__ R2, ST *
         const A s = x2 + k2 < n2 ? sf[x2 + k2] : M::id();
         T[(int64_t)x1 * n2 + x2] = M::template put<ST>(M::op(t2, M::op(hv[x2], s)));
     }
+}
+
+template <class M, class SR = typename M::car_t, class ST = typename M::car_t>
+__global__ void __launch_bounds__(256)
+k_exc2d(const SR *__restrict__ R, const typename M::car_t *__restrict__ R2, ST *__restrict__ T, int n1,
+        int n2, int k1, int k2)
+{
+    k_exc2d_body<M, SR, ST>(R, R2, T, n1, n2, k1, k2, blockIdx.x, gridDim.x);
 }
 
 }  // namespace exsum

@@ -316,11 +316,13 @@ k_rowx_bulk(const typename M::loc_t *__restrict__ in, const typename M::car_t *_
     if (tid < 4) idc[tid] = M::lid();
     // W: columns [L, LP) of every row (strip padding of the row phase;
     // none when the row length is fixed at compile time)
-    if (LT == 0 && LP > L) {
-        const int padw = LP - L;
-        for (int i = tid; i < TR * padw; i += NT) {
-            const int r = i / padw;
-            W[r * LSW + tswz<Lt>(L + (i - r * padw))] = M::lid();
+    if constexpr (LT == 0) {
+        if (LP > L) {
+            const int padw = LP - L;
+            for (int i = tid; i < TR * padw; i += NT) {
+                const int r = i / padw;
+                W[r * LSW + tswz<Lt>(L + (i - r * padw))] = M::lid();
+            }
         }
     }
     // staging rows past the halo (read by the walk, never copied into)

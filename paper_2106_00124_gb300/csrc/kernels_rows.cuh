@@ -67,16 +67,15 @@ __device__ __forceinline__ SOut finish(const typename M::acc_t &t, typename M::l
 // rows (a grid of a few blocks per SM).
 // ---------------------------------------------------------------------------
 template <class M, class SIn, int LPR>
-__global__ void __launch_bounds__(256)
-k_row_totals(const SIn *__restrict__ X, typename M::car_t *__restrict__ R, int64_t rows, int L)
+__device__ __forceinline__ void k_row_totals_body(const SIn *__restrict__ X, typename M::car_t *__restrict__ R, int64_t rows, int L, int64_t vbid, int64_t vgrid)
 {
     using Lt = typename M::loc_t;
     constexpr int RPW = 32 / LPR;
     constexpr int RU = 4;  // row groups in flight per warp
     const int lane = threadIdx.x & 31;
     const int sub = lane & (LPR - 1);
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t warp = ((int64_t)vbid * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)vgrid * blockDim.x) >> 5;
     const uint64_t pol = l2_policy_evict_last();  // the first pass reads X too
     constexpr size_t VALIGN = sizeof(SIn) * 4 >= 16 ? 16 : sizeof(SIn) * 4;
     const bool vec = (L % 4 == 0) && ((((uintptr_t)X) & (VALIGN - 1)) == 0);
@@ -126,6 +125,13 @@ k_row_totals(const SIn *__restrict__ X, typename M::car_t *__restrict__ R, int64
             if (sub == 0 && r < rows) R[r] = M::template put<typename M::car_t>(M::widen(acc[u]));
         }
     }
+}
+
+template <class M, class SIn, int LPR>
+__global__ void __launch_bounds__(256)
+k_row_totals(const SIn *__restrict__ X, typename M::car_t *__restrict__ R, int64_t rows, int L)
+{
+    k_row_totals_body<M, SIn, LPR>(X, R, rows, L, blockIdx.x, gridDim.x);
 }
 
 // Suffix-buffer index: 4 spare slots per 32 elements, so that 16-byte
@@ -201,10 +207,9 @@ __device__ __forceinline__ void smem_walk(typename M::loc_t *col, int LS, int k,
 // the scalar reads).  Each output is T[row] (+) prefix (+) suffix.
 // ---------------------------------------------------------------------------
 template <class M, class SIn, class SOut, int KMAX, int EPL>
-__global__ void __launch_bounds__(256)
-k_rowx(const SIn *__restrict__ in, const typename M::car_t *__restrict__ T,
+__device__ __forceinline__ void k_rowx_body(const SIn *__restrict__ in, const typename M::car_t *__restrict__ T,
        const typename M::car_t *__restrict__ R1, int k1, SOut *__restrict__ out, int64_t O, int n2,
-       int L, int k2, int k3, int TR, int GO, int ntile, int RS, int RSA, int LS, int lpr)
+       int L, int k2, int k3, int TR, int GO, int ntile, int RS, int RSA, int LS, int lpr, int64_t vbid, int64_t vgrid)
 {
     using Lt = typename M::loc_t;
     using A = typename M::acc_t;
@@ -215,8 +220,8 @@ k_rowx(const SIn *__restrict__ in, const typename M::car_t *__restrict__ T,
     const int LPs = L32 + 4 * (L32 >> 5) + 4;
     const int rpw = 32 / lpr;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t og = blockIdx.x / ntile;
-    const int a = (int)(blockIdx.x - og * ntile) * TR;
+    const int64_t og = vbid / ntile;
+    const int a = (int)(vbid - og * ntile) * TR;
     const int64_t o0 = og * GO;
     const int ng = (int)min((int64_t)GO, O - o0);  // slices in this block
     const int rend = min(a + TR, n2);
@@ -486,6 +491,15 @@ k_rowx(const SIn *__restrict__ in, const typename M::car_t *__restrict__ T,
             __syncwarp();
         }
     }
+}
+
+template <class M, class SIn, class SOut, int KMAX, int EPL>
+__global__ void __launch_bounds__(256)
+k_rowx(const SIn *__restrict__ in, const typename M::car_t *__restrict__ T,
+       const typename M::car_t *__restrict__ R1, int k1, SOut *__restrict__ out, int64_t O, int n2,
+       int L, int k2, int k3, int TR, int GO, int ntile, int RS, int RSA, int LS, int lpr)
+{
+    k_rowx_body<M, SIn, SOut, KMAX, EPL>(in, T, R1, k1, out, O, n2, L, k2, k3, TR, GO, ntile, RS, RSA, LS, lpr, blockIdx.x, gridDim.x);
 }
 
 }  // namespace exsum
