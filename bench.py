@@ -664,6 +664,7 @@ def batched_bench(count, seed=11, steps=20, warmup=3, plain_steps=3):
     tune_s = time.perf_counter() - t0
     assert rc == 0, ex.strerror(rc)
     _, lanes, order, wsb, kernels = ex.exsum_batch_info(plan)
+    _, mode, nlevel, lc, inter, tpv, tall, persist = ex.exsum_batch_schedule(plan)
     for _ in range(max(1, warmup)):
         ex.exsum_batch_launch(plan, stream.cuda_stream)
     torch.cuda.synchronize()
@@ -694,6 +695,13 @@ def batched_bench(count, seed=11, steps=20, warmup=3, plain_steps=3):
     plain_ms = a.elapsed_time(b) / plain_steps
     ex.exsum_batch_launch(plan, sp)
     torch.cuda.synchronize()
+    # the plain launches' results (checked against the oracle by the tests)
+    # against the plan's: equal bits on lanes, within the fp32 bound on levels
+    rel = 0.0
+    for r_, o in zip(ref, outs[:8]):
+        r64, o64 = r_.double(), o.double()
+        scale = torch.clamp(r64.abs(), min=float(torch.sqrt(torch.mean(r64 * r64))))
+        rel = max(rel, float(((o64 - r64).abs() / scale).max()))
     same = all(torch.equal(r_, o) for r_, o in zip(ref, outs[:8]))
     ex.exsum_batch_destroy(plan)
     return {
@@ -702,10 +710,14 @@ def batched_bench(count, seed=11, steps=20, warmup=3, plain_steps=3):
         "plain_value": round(total / (plain_ms * 1e-3) / 1e9, 3),
         "speedup_vs_plain": round(plain_ms / batch_ms, 3), "ms_per_batch": round(batch_ms, 3),
         "plain_ms_per_batch": round(plain_ms, 3), "tensors": len(spec), "elements": total,
-        "schedule": {"lanes": lanes, "order": ["lpt", "round_robin"][order],
-                     "kernels_per_launch": kernels, "lane_workspace_bytes": wsb,
+        "schedule": {"mode": ["lanes", "levels"][mode], "level_tensors": nlevel,
+                     "lanes": lanes, "order": ["lpt", "round_robin"][order],
+                     "level_tune": {"lc": lc, "interleave": inter, "tiles_per_vb": tpv, "tall": tall,
+                                    "persist": persist},
+                     "kernels_per_launch": kernels, "workspace_bytes": wsb,
                      "autotune_s": round(tune_s, 2)},
-        "identical_to_plain": same, "dtype": "f32", "data": "synthetic (seeded, on device)",
+        "identical_to_plain": same, "max_rel_diff_vs_plain": rel,
+        "dtype": "f32", "data": "synthetic (seeded, on device)",
         "config": {"workload": "batched_%d_uneven_d2d3_f32_add" % count,
                    "sides": [32, 512], "k": [2, 32], "cap": 1 << 24},
         "plain": "the same tensors, one exsum_excluded_ws call each on one stream"}

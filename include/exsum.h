@@ -201,28 +201,52 @@ typedef struct exsum_batch exsum_batch;
 /*
  * Plans the excluded sums of `count` tensors as ONE CUDA graph.  Every
  * descriptor is validated as for exsum_excluded (EXSUM_EINVAL otherwise).
- * The tensors are assigned to `lanes` concurrent streams -- longest
- * processing time first (order 0) or round-robin by size (order 1) -- each
- * lane with one workspace sized for its largest tensor (allocated here with
- * cudaMalloc), and the whole batch is captured into a graph bound to the
- * descriptors' pointers.  lanes <= 0 autotunes: each candidate schedule (1..32
- * lanes, both orders) is captured and its replays timed on the device
- * (inputs are read and outputs written during tuning), and the fastest is
- * kept; the choice is remembered per batch signature (shapes, boxes, ops,
- * dtypes) for the process and, if the environment variable EXSUM_TUNE_CACHE
- * names a file, appended there and read back by later processes.  `stream`
- * must not be capturing (EXSUM_EBUSY).  On success *plan owns the graph and
- * the lane workspaces until exsum_batch_destroy.
+ * Two schedules:
+ *   levels  every tensor whose excluded sum takes the row schedule with the
+ *           two-dimensional lower problem (d = 3; Sec. 4) or the small d = 2
+ *           path, with fp32 +, joins a level set: each pass level of all
+ *           those tensors is ONE launch (per register class) whose blocks
+ *           take (tensor, pass, tile) items from a device work list -- at
+ *           most nine kernels and one memset per replay, whatever the
+ *           batch size.
+ *           The other tensors run on one lane beside it;
+ *   lanes   the tensors are assigned to `lanes` concurrent streams --
+ *           longest processing time first (order 0) or round-robin by size
+ *           (order 1) -- each lane with one workspace sized for its largest
+ *           tensor, every tensor with its own chain of kernels.
+ * lanes > 0 picks the lanes schedule with that many streams, lanes ==
+ * EXSUM_BATCH_LEVELS the level schedule with its default tuning, and
+ * lanes == 0 autotunes: candidate schedules (levels with several strided
+ * chunk lengths, row-total placements, final-pass tiles per block and tile
+ * heights; lanes with 1..32 streams and both orders) are captured and their
+ * replays timed on the device (inputs are read and outputs written during
+ * tuning), and the fastest is kept; the choice is remembered per batch
+ * signature (shapes, boxes, ops, dtypes) for the process and, if the
+ * environment variable EXSUM_TUNE_CACHE names a file, appended there and
+ * read back by later processes.  Workspaces are allocated here with
+ * cudaMalloc.  `stream` must not be capturing (EXSUM_EBUSY).  On success
+ * *plan owns the graph and the workspaces until exsum_batch_destroy.
  */
+#define EXSUM_BATCH_LEVELS (-1)
 int exsum_batch_create(const exsum_desc *descs, int count, int lanes, void *stream,
                        exsum_batch **plan);
 
 /* Launches the planned batch on `stream` (one cudaGraphLaunch). */
 int exsum_batch_launch(exsum_batch *plan, void *stream);
 
-/* Schedule of a plan: lanes, order, total lane workspace bytes, kernels per launch. */
+/* Schedule of a plan: lanes, order, total workspace bytes, kernels per launch. */
 int exsum_batch_info(const exsum_batch *plan, int *lanes, int *order, size_t *workspace_bytes,
                      int64_t *kernels);
+
+/* The rest of the schedule (any pointer may be NULL): mode (0 lanes, 1
+ * levels), tensors in the level set, and the level tuning: rows per strided
+ * chunk (0: sized per tensor), row totals interleaved with the strided
+ * chunks over the same rows (1) or after them (0), tiles per virtual block
+ * of the bulk final pass, tall (1) or per-tensor (0) k_rowx tiles, and
+ * persistent grids pulling work-list slots from a counter (1) or one block
+ * per slot (0). */
+int exsum_batch_schedule(const exsum_batch *plan, int *mode, int *level_tensors, int *lc, int *interleave,
+                         int *tiles_per_vb, int *tall, int *persist);
 
 /* Waits for the device, then frees the plan's graph and workspaces. */
 void exsum_batch_destroy(exsum_batch *plan);

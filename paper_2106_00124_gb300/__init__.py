@@ -66,6 +66,7 @@ def make_desc(in_ptr, out_ptr, shape, k, op, dtype):
 
 
 SERVE_HOST = 1
+BATCH_LEVELS = -1
 
 _P = ctypes.c_void_p
 _I64P = ctypes.POINTER(ctypes.c_int64)
@@ -106,6 +107,7 @@ _SIG = {
     "exsum_batch_info": ([_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                           ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_int64)],
                          ctypes.c_int),
+    "exsum_batch_schedule": ([_P] + [ctypes.POINTER(ctypes.c_int)] * 7, ctypes.c_int),
     "exsum_batch_destroy": ([_P], None),
     "exsum_server_create": ([ctypes.c_size_t, ctypes.c_int], _P),
     "exsum_server_submit": ([_P, ctypes.POINTER(exsum_desc), ctypes.c_int,
@@ -291,6 +293,13 @@ def exsum_batch_info(plan):
     rc = _load().exsum_batch_info(plan, ctypes.byref(lanes), ctypes.byref(order), ctypes.byref(ws),
                                   ctypes.byref(ker))
     return rc, lanes.value, order.value, ws.value, ker.value
+
+
+def exsum_batch_schedule(plan):
+    """(status, mode, level_tensors, lc, interleave, tiles_per_vb, tall, persist); mode 0 lanes, 1 levels."""
+    v = [ctypes.c_int() for _ in range(7)]
+    rc = _load().exsum_batch_schedule(plan, *[ctypes.byref(x) for x in v])
+    return (rc,) + tuple(x.value for x in v)
 
 
 def exsum_batch_destroy(plan):

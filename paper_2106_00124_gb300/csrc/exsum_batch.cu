@@ -1,16 +1,17 @@
 // exsum_batch.cu -- excluded sums of a batch of uneven tensors as one CUDA
 // graph launch, with an autotuned schedule.
 //
-// A plan assigns the tensors of the batch to `lanes` concurrent streams
-// (longest-processing-time first, or round-robin in size order), gives every
-// lane one workspace sized for its largest tensor (a lane runs its tensors
-// one after another, so they share it), and captures the whole batch --
-// every pass of every tensor, with each tensor's own side-stream branches --
-// into one CUDA graph that is launched with a single call.  The autotuner
-// captures one graph per candidate schedule (lane counts 1..32, both
-// orders), times a few replays of each and keeps the fastest; its choice is
-// remembered per batch signature in memory and, when EXSUM_TUNE_CACHE names
-// a file, across processes.
+// Two schedules.  Levels (exsum_level.cu): the tensors the level kernels
+// take run as one persistent launch per pass level, the rest on one lane
+// beside it.  Lanes: the tensors are assigned to `lanes` concurrent streams
+// (longest-processing-time first, or round-robin in size order), every lane
+// gets one workspace sized for its largest tensor (a lane runs its tensors
+// one after another, so they share it), and every pass of every tensor, with
+// each tensor's own side-stream branches, is captured into the graph.  The
+// autotuner captures one graph per candidate schedule, times a few replays
+// of each and keeps the fastest; its choice is remembered per batch
+// signature in memory and, when EXSUM_TUNE_CACHE names a file, across
+// processes.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -22,6 +23,7 @@
 #include <vector>
 
 #include "../../include/exsum.h"
+#include "level.h"
 
 namespace exsum {
 const void *aux_prepare(void *stream);   // exsum_abi.cu: side streams of a caller stream
@@ -29,10 +31,14 @@ const void *aux_prepare(void *stream);   // exsum_abi.cu: side streams of a call
 
 struct exsum_batch {
     int count = 0;
+    int mode = 0;                          // 0: lanes, 1: levels
     int lanes = 0;
     int order = 0;                         // 0: LPT, 1: round-robin by size
+    exsum::LevelTune tune;
     std::vector<exsum_desc> descs;
-    std::vector<int> lane_of;              // tensor -> lane
+    std::vector<int> level_idx;            // tensors in the level set
+    exsum::LevelSet *level = nullptr;
+    std::vector<int> lane_of;              // tensor -> lane (-1: level set)
     std::vector<std::vector<int>> lane_items;
     std::vector<void *> lane_ws;
     std::vector<size_t> lane_ws_bytes;
@@ -47,8 +53,15 @@ struct exsum_batch {
 
 namespace {
 
+// A schedule: mode, lanes/order (lanes mode, and the lane of the level
+// mode's other tensors), level tuning.
+struct Sched {
+    int mode = 0, lanes = 1, order = 0;
+    exsum::LevelTune tune;
+};
+
 std::mutex g_tune_mu;
-std::map<std::string, std::pair<int, int>> g_tuned;   // signature -> (lanes, order)
+std::map<std::string, Sched> g_tuned;   // signature -> schedule
 
 std::string signature(const exsum_desc *descs, int count)
 {
@@ -75,6 +88,9 @@ std::string signature(const exsum_desc *descs, int count)
     return buf;
 }
 
+// Cache file lines: "<signature> <mode> <lanes> <order> <lc> <interleave>
+// <tiles_per_vb> <tall> <persist>"; lines of an older format (three fields:
+// lanes schedules only) are read as lanes schedules.
 void load_tune_file()
 {
     static bool loaded = false;
@@ -84,19 +100,43 @@ void load_tune_file()
     if (!path) return;
     FILE *f = fopen(path, "r");
     if (!f) return;
-    char key[64];
-    int lanes, order;
-    while (fscanf(f, "%63s %d %d", key, &lanes, &order) == 3) g_tuned[key] = {lanes, order};
+    char line[256];
+    while (fgets(line, sizeof(line), f)) {
+        char key[64];
+        Sched sc;
+        int v[8];
+        const int got = sscanf(line, "%63s %d %d %d %d %d %d %d %d", key, &v[0], &v[1], &v[2], &v[3], &v[4],
+                               &v[5], &v[6], &v[7]);
+        if (got == 9) {
+            sc.mode = v[0];
+            sc.lanes = v[1];
+            sc.order = v[2];
+            sc.tune.lc = v[3];
+            sc.tune.interleave = v[4];
+            sc.tune.tiles_per_vb = v[5];
+            sc.tune.tall = v[6];
+            sc.tune.persist = v[7];
+        } else if (got == 3) {
+            sc.mode = 0;
+            sc.lanes = v[0];
+            sc.order = v[1];
+        } else {
+            continue;
+        }
+        if (sc.lanes < 1) continue;
+        g_tuned[key] = sc;
+    }
     fclose(f);
 }
 
-void save_tune_entry(const std::string &key, int lanes, int order)
+void save_tune_entry(const std::string &key, const Sched &sc)
 {
     const char *path = getenv("EXSUM_TUNE_CACHE");
     if (!path) return;
     FILE *f = fopen(path, "a");
     if (!f) return;
-    fprintf(f, "%s %d %d\n", key.c_str(), lanes, order);
+    fprintf(f, "%s %d %d %d %d %d %d %d %d\n", key.c_str(), sc.mode, sc.lanes, sc.order, sc.tune.lc,
+            sc.tune.interleave, sc.tune.tiles_per_vb, sc.tune.tall, sc.tune.persist);
     fclose(f);
 }
 
@@ -118,6 +158,8 @@ void destroy_graph(exsum_batch *p)
 void release(exsum_batch *p)
 {
     destroy_graph(p);
+    exsum::level_destroy(p->level);
+    p->level = nullptr;
     for (void *w : p->lane_ws)
         if (w) cudaFree(w);
     for (cudaEvent_t e : p->lane_join)
@@ -133,33 +175,43 @@ void release(exsum_batch *p)
     p->cap = nullptr;
 }
 
-// Assigns tensors to lanes and sizes the lane workspaces.
-int schedule(exsum_batch *p, int lanes, int order)
+// Splits the batch between the level set (level mode) and the lanes, assigns
+// the lanes' tensors to lanes and sizes the lane workspaces.
+int schedule(exsum_batch *p, const Sched &sc)
 {
     const int n = p->count;
-    std::vector<int> idx(n);
-    for (int i = 0; i < n; ++i) idx[i] = i;
+    p->mode = sc.mode;
+    p->tune = sc.tune;
+    p->order = sc.order;
+    p->level_idx.clear();
+    p->lane_of.assign(n, -1);
+    std::vector<int> idx;
+    for (int i = 0; i < n; ++i) {
+        if (sc.mode == 1 && exsum::level_accepts(p->descs[i], exsum::level_sms()))
+            p->level_idx.push_back(i);
+        else
+            idx.push_back(i);
+    }
+    const int lanes = std::max(1, std::min(sc.lanes, (int)idx.size()));
     std::stable_sort(idx.begin(), idx.end(),
                      [&](int a, int b) { return elems(p->descs[a]) > elems(p->descs[b]); });
-    p->lanes = lanes;
-    p->order = order;
-    p->lane_items.assign(lanes, {});
-    p->lane_of.assign(n, 0);
-    std::vector<int64_t> load(lanes, 0);
-    for (int j = 0; j < n; ++j) {
+    p->lanes = idx.empty() ? 0 : lanes;
+    p->lane_items.assign(p->lanes, {});
+    std::vector<int64_t> load(p->lanes, 0);
+    for (size_t j = 0; j < idx.size(); ++j) {
         const int t = idx[j];
         int lane;
-        if (order == 0) {
+        if (sc.order == 0) {
             lane = (int)(std::min_element(load.begin(), load.end()) - load.begin());
         } else {
-            lane = j % lanes;
+            lane = (int)(j % p->lanes);
         }
         load[lane] += elems(p->descs[t]);
         p->lane_items[lane].push_back(t);
         p->lane_of[t] = lane;
     }
-    p->lane_ws_bytes.assign(lanes, 0);
-    for (int t = 0; t < n; ++t) {
+    p->lane_ws_bytes.assign(p->lanes, 0);
+    for (int t : idx) {
         const exsum_desc &d = p->descs[t];
         int st = 0;
         const size_t b = exsum_workspace_bytes(d.d, d.shape, d.k, d.op, d.dtype, 1, &st);
@@ -170,12 +222,17 @@ int schedule(exsum_batch *p, int lanes, int order)
     return EXSUM_OK;
 }
 
-// Allocates lane resources and captures the batch into a graph.
+// Allocates the plan's resources and captures the batch into a graph.
 int build(exsum_batch *p)
 {
     cudaError_t e = cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming);
     if (e != cudaSuccess) return EXSUM_ECUDA;
+    if (!p->level_idx.empty()) {
+        const int rc = exsum::level_create(p->descs.data(), p->level_idx.data(), (int)p->level_idx.size(), p->tune,
+                                           &p->level);
+        if (rc) return rc;
+    }
     p->lane_streams.assign(p->lanes, nullptr);
     p->lane_join.assign(p->lanes, nullptr);
     p->lane_ws.assign(p->lanes, nullptr);
@@ -202,13 +259,17 @@ int build(exsum_batch *p)
                                    p->lane_ws_bytes[l], p->lane_streams[l]);
             if (rc) break;
         }
+    }
+    // the level set on the capture stream itself, beside the lanes
+    if (rc == EXSUM_OK && p->level) rc = exsum::level_enqueue(p->level, p->cap);
+    for (int l = 0; l < p->lanes; ++l) {
         cudaEventRecord(p->lane_join[l], p->lane_streams[l]);
         cudaStreamWaitEvent(p->cap, p->lane_join[l], 0);
     }
     e = cudaStreamEndCapture(p->cap, &p->graph);
     if (rc) return rc;
     if (e != cudaSuccess) return EXSUM_ECUDA;
-    p->kernels = exsum_launch_count() - launches0;
+    p->kernels = exsum_launch_count() - launches0 + exsum::level_kernels(p->level);
     // honour the per-node priorities of the side branches (see exsum_graph_instantiate)
     e = cudaGraphInstantiateWithFlags(&p->exec, p->graph, cudaGraphInstantiateFlagUseNodePriority);
     if (e != cudaSuccess) {
@@ -236,8 +297,119 @@ float time_replays(exsum_batch *p, cudaStream_t s, int reps)
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
+    if (cudaGetLastError() != cudaSuccess) return 3.4e38f;
     std::sort(t.begin(), t.end());
     return t[t.size() / 2];
+}
+
+// Builds and times one candidate; returns its median replay time in ms,
+// or a huge value (rc set) if it could not be built.
+float try_schedule(const exsum_desc *descs, int count, const Sched &sc, int *rc_out)
+{
+    exsum_batch trial;
+    trial.count = count;
+    trial.descs.assign(descs, descs + count);
+    int rc = schedule(&trial, sc);
+    if (!rc) rc = build(&trial);
+    float ms = 3.4e38f;
+    if (!rc) ms = time_replays(&trial, trial.cap, 3);
+    release(&trial);
+    *rc_out = rc;
+    return ms;
+}
+
+// Autotuning: lanes schedules (1..32 lanes, both orders) and, when some
+// tensors join a level set, level schedules by coordinate descent over the
+// strided chunk length, the row-total placement, the bulk tiles per
+// virtual block and the k_rowx tile height, from the defaults.
+int autotune(const exsum_desc *descs, int count, Sched *best_out)
+{
+    float best = 3.4e38f;
+    Sched best_sc;
+    auto consider = [&](const Sched &sc) -> int {
+        int rc = 0;
+        const float ms = try_schedule(descs, count, sc, &rc);
+        if (rc == EXSUM_ENOMEM) return EXSUM_OK;   // does not fit: skip
+        if (rc) return rc;
+        if (ms < best) {
+            best = ms;
+            best_sc = sc;
+        }
+        return EXSUM_OK;
+    };
+    const int cands[] = {1, 2, 4, 8, 16, 32};
+    for (int c : cands) {
+        if (c > count) break;
+        for (int ord = 0; ord < 2; ++ord) {
+            if (c == 1 && ord == 1) continue;
+            Sched sc;
+            sc.mode = 0;
+            sc.lanes = c;
+            sc.order = ord;
+            const int rc = consider(sc);
+            if (rc) return rc;
+        }
+    }
+    int accepted = 0;
+    for (int t = 0; t < count; ++t) accepted += exsum::level_accepts(descs[t], exsum::level_sms()) ? 1 : 0;
+    if (accepted > 0) {
+        Sched cur;
+        cur.mode = 1;
+        cur.lanes = std::min(4, std::max(1, count - accepted));
+        float cur_ms = 3.4e38f;
+        {
+            const float b0 = best;
+            const int rc = consider(cur);
+            if (rc) return rc;
+            if (best < b0) cur_ms = best;
+        }
+        // one field at a time, keeping each improvement
+        auto step = [&](Sched s2) -> int {
+            const float b0 = best;
+            const int rc = consider(s2);
+            if (rc) return rc;
+            if (best < b0 && best < cur_ms) {
+                cur = s2;
+                cur_ms = best;
+            }
+            return EXSUM_OK;
+        };
+        const Sched base_lc = cur;
+        for (int v : {32, 64, 128}) {
+            Sched s2 = base_lc;
+            s2.tune.lc = v;
+            const int rc = step(s2);
+            if (rc) return rc;
+        }
+        {
+            Sched s2 = cur;
+            s2.tune.interleave = 1 - cur.tune.interleave;
+            const int rc = step(s2);
+            if (rc) return rc;
+        }
+        const Sched base_tpv = cur;
+        for (int v : {1, 4}) {
+            Sched s2 = base_tpv;
+            s2.tune.tiles_per_vb = v;
+            const int rc = step(s2);
+            if (rc) return rc;
+        }
+        {
+            Sched s2 = cur;
+            s2.tune.tall = 1 - cur.tune.tall;
+            const int rc = step(s2);
+            if (rc) return rc;
+        }
+        {
+            Sched s2 = cur;
+            s2.tune.persist = 1 - cur.tune.persist;
+            const int rc = step(s2);
+            if (rc) return rc;
+        }
+    }
+    if (best >= 3.4e38f) return EXSUM_ENOMEM;
+    *best_out = best_sc;
+    return EXSUM_OK;
 }
 
 }  // namespace
@@ -247,7 +419,7 @@ extern "C" {
 int exsum_batch_create(const exsum_desc *descs, int count, int lanes, void *stream,
                        exsum_batch **plan)
 {
-    if (!plan || !descs || count < 1) return EXSUM_EINVAL;
+    if (!plan || !descs || count < 1 || lanes < EXSUM_BATCH_LEVELS) return EXSUM_EINVAL;
     *plan = nullptr;
     for (int t = 0; t < count; ++t) {
         const exsum_desc &d = descs[t];
@@ -260,53 +432,37 @@ int exsum_batch_create(const exsum_desc *descs, int count, int lanes, void *stre
     if (cudaStreamIsCapturing((cudaStream_t)stream, &cs) != cudaSuccess ||
         cs != cudaStreamCaptureStatusNone)
         return EXSUM_EBUSY;
-    const std::string key = signature(descs, count);
-    int order = 0;
-    if (lanes <= 0) {
-        std::lock_guard<std::mutex> lock(g_tune_mu);
-        load_tune_file();
-        auto it = g_tuned.find(key);
-        if (it != g_tuned.end()) {
-            lanes = it->second.first;
-            order = it->second.second;
-        }
-    }
-    if (lanes <= 0) {
-        // Autotune: capture each candidate schedule, time its replays, keep the best.
-        float best = 3.4e38f;
-        int best_lanes = 1, best_order = 0;
-        const int cands[] = {1, 2, 4, 8, 16, 32};
-        for (int c : cands) {
-            if (c > count) break;
-            for (int ord = 0; ord < 2; ++ord) {
-                if (c == 1 && ord == 1) continue;
-                exsum_batch trial;
-                trial.count = count;
-                trial.descs.assign(descs, descs + count);
-                int rc = schedule(&trial, c, ord);
-                if (!rc) rc = build(&trial);
-                float ms = 3.4e38f;
-                if (!rc) ms = time_replays(&trial, trial.cap, 3);
-                release(&trial);
-                if (rc == EXSUM_ENOMEM) continue;
-                if (rc) return rc;
-                if (ms < best) {
-                    best = ms;
-                    best_lanes = c;
-                    best_order = ord;
-                }
+    Sched sc;
+    if (lanes > 0) {
+        sc.mode = 0;
+        sc.lanes = lanes;
+    } else if (lanes == EXSUM_BATCH_LEVELS) {
+        sc.mode = 1;
+        sc.lanes = 4;
+    } else {
+        const std::string key = signature(descs, count);
+        bool found = false;
+        {
+            std::lock_guard<std::mutex> lock(g_tune_mu);
+            load_tune_file();
+            auto it = g_tuned.find(key);
+            if (it != g_tuned.end()) {
+                sc = it->second;
+                found = true;
             }
         }
-        lanes = best_lanes;
-        order = best_order;
-        std::lock_guard<std::mutex> lock(g_tune_mu);
-        g_tuned[key] = {lanes, order};
-        save_tune_entry(key, lanes, order);
+        if (!found) {
+            const int rc = autotune(descs, count, &sc);
+            if (rc) return rc;
+            std::lock_guard<std::mutex> lock(g_tune_mu);
+            g_tuned[key] = sc;
+            save_tune_entry(key, sc);
+        }
     }
     exsum_batch *p = new exsum_batch();
     p->count = count;
     p->descs.assign(descs, descs + count);
-    int rc = schedule(p, std::min(lanes, count), order);
+    int rc = schedule(p, sc);
     if (!rc) rc = build(p);
     if (rc) {
         release(p);
@@ -335,11 +491,25 @@ int exsum_batch_info(const exsum_batch *plan, int *lanes, int *order, size_t *wo
     if (lanes) *lanes = plan->lanes;
     if (order) *order = plan->order;
     if (workspace_bytes) {
-        size_t b = 0;
+        size_t b = exsum::level_workspace_bytes(plan->level);
         for (size_t x : plan->lane_ws_bytes) b += x;
         *workspace_bytes = b;
     }
     if (kernels) *kernels = plan->kernels;
+    return EXSUM_OK;
+}
+
+int exsum_batch_schedule(const exsum_batch *plan, int *mode, int *level_tensors, int *lc, int *interleave,
+                         int *tiles_per_vb, int *tall, int *persist)
+{
+    if (!plan) return EXSUM_EINVAL;
+    if (mode) *mode = plan->mode;
+    if (level_tensors) *level_tensors = (int)plan->level_idx.size();
+    if (lc) *lc = plan->tune.lc;
+    if (interleave) *interleave = plan->tune.interleave;
+    if (tiles_per_vb) *tiles_per_vb = plan->tune.tiles_per_vb;
+    if (tall) *tall = plan->tune.tall;
+    if (persist) *persist = plan->tune.persist;
     return EXSUM_OK;
 }
 

@@ -52,6 +52,11 @@ __device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count)
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count) : "memory");
 }
 
+__device__ __forceinline__ void mbar_inval(uint64_t *bar)
+{
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];\n" ::"r"(smem_addr(bar)) : "memory");
+}
+
 // Makes the initialised barriers visible to the bulk-copy (async) proxy.
 __device__ __forceinline__ void mbar_fence_init()
 {
@@ -284,10 +289,10 @@ __device__ __forceinline__ void rowbulk_walk(const typename M::loc_t *__restrict
 // returns (never expected).
 // ---------------------------------------------------------------------------
 template <class M, class SOut, int KMAX, int EPL, int NBUF, int NT, int LT>
-__global__ void __launch_bounds__(NT, 512 / NT)
-k_rowx_bulk(const typename M::loc_t *__restrict__ in, const typename M::car_t *__restrict__ T,
-            SOut *__restrict__ out, int ntiles, int ntile, int n2, int L_, int k2, int k3, int TR,
-            int LSW_, int lpr_, int aligned)
+__device__ __forceinline__ bool
+k_rowx_bulk_body(const typename M::loc_t *__restrict__ in, const typename M::car_t *__restrict__ T,
+                 SOut *__restrict__ out, int ntiles, int ntile, int n2, int L_, int k2, int k3, int TR,
+                 int LSW_, int lpr_, int aligned, int64_t vbid, int64_t vgrid)
 {
     const int L = LT > 0 ? LT : L_;
     const int LSW = LT > 0 ? LT : LSW_;
@@ -310,7 +315,8 @@ k_rowx_bulk(const typename M::loc_t *__restrict__ in, const typename M::car_t *_
     const uint64_t pol_in = l2_policy_evict_first();
     const uint64_t pol_out = l2_policy_evict_first();
     const int halo = k2 > 1 ? k2 - 1 : 0;
-    const int grid = (int)gridDim.x;
+    const int grid = (int)vgrid;
+    const int bid = (int)vbid;
 
     // ---- one-time set-up: identity that no tile overwrites ----
     if (tid < 4) idc[tid] = M::lid();
@@ -377,8 +383,8 @@ k_rowx_bulk(const typename M::loc_t *__restrict__ in, const typename M::car_t *_
     // tile coordinates (slice, tile in slice) of this block's current tile
     // and of the next tile to stage; a step of `grid` tiles is (go, gj)
     const int go = grid / ntile, gj = grid - go * ntile;
-    int o_cur = (int)blockIdx.x / ntile;
-    int j_cur = (int)blockIdx.x - o_cur * ntile;
+    int o_cur = bid / ntile;
+    int j_cur = bid - o_cur * ntile;
     int o_nx = o_cur, j_nx = j_cur;
     auto step = [&](int &oo, int &jj) {
         oo += go;
@@ -389,7 +395,7 @@ k_rowx_bulk(const typename M::loc_t *__restrict__ in, const typename M::car_t *_
         }
     };
     for (int b = 0; b < NBUF; ++b) {
-        if ((int)blockIdx.x + b * grid < ntiles) issue(o_nx, j_nx * TR, b);
+        if (bid + b * grid < ntiles) issue(o_nx, j_nx * TR, b);
         step(o_nx, j_nx);
     }
 
@@ -416,7 +422,7 @@ k_rowx_bulk(const typename M::loc_t *__restrict__ in, const typename M::car_t *_
     const int coff_o = 4 * (lane ^ ((lane >> 3) + 4));
 
     int it = 0;
-    for (int t = blockIdx.x; t < ntiles; t += grid, ++it, step(o_cur, j_cur)) {
+    for (int t = bid; t < ntiles; t += grid, ++it, step(o_cur, j_cur)) {
         const int b = NBUF == 1 ? 0 : it % NBUF;
         const unsigned parity = (unsigned)(it / NBUF) & 1u;
         const int o = o_cur;
@@ -427,7 +433,7 @@ k_rowx_bulk(const typename M::loc_t *__restrict__ in, const typename M::car_t *_
         if (tid == 0) ok = mbar_wait_bounded(bar + b, parity) ? 1 : 0;
         if (!__syncthreads_and(ok)) {
             if (tid == 0) atomicAdd(&g_wait_timeouts, 1u);
-            return;
+            return false;
         }
         // ---- window along n2: stage -> W ----
 #pragma unroll
@@ -549,6 +555,21 @@ k_rowx_bulk(const typename M::loc_t *__restrict__ in, const typename M::car_t *_
         }
         __syncthreads();   // W is rewritten by the next tile's walk
     }
+    // every copy issued was waited for: the barriers can be retired, so that
+    // a later call of this body in the same block may initialise them again
+    if (tid == 0)
+        for (int b = 0; b < NBUF; ++b) mbar_inval(bar + b);
+    return true;
+}
+
+template <class M, class SOut, int KMAX, int EPL, int NBUF, int NT, int LT>
+__global__ void __launch_bounds__(NT, 512 / NT)
+k_rowx_bulk(const typename M::loc_t *__restrict__ in, const typename M::car_t *__restrict__ T,
+            SOut *__restrict__ out, int ntiles, int ntile, int n2, int L_, int k2, int k3, int TR,
+            int LSW_, int lpr_, int aligned)
+{
+    k_rowx_bulk_body<M, SOut, KMAX, EPL, NBUF, NT, LT>(in, T, out, ntiles, ntile, n2, L_, k2, k3, TR, LSW_, lpr_,
+                                                     aligned, blockIdx.x, gridDim.x);
 }
 
 }  // namespace exsum

@@ -506,8 +506,10 @@ struct Pipe {
     // tallest tile (at most 64 rows, a multiple of the rows one row pass
     // covers and of the walk's segments) that lets two blocks share an SM,
     // else one staging buffer, else one block per SM.  EXSUM_ROWX_TR and
-    // EXSUM_ROWX_NBUF override (tuning).
-    static BulkPlan bulk_plan(int64_t L, int64_t n2, int64_t O2, int kk, int kmax, int64_t sms)
+    // EXSUM_ROWX_NBUF override (tuning), and nbuf_force / tr_force override
+    // those.
+    static BulkPlan bulk_plan(int64_t L, int64_t n2, int64_t O2, int kk, int kmax, int64_t sms,
+                              int nbuf_force = 0, int tr_force = 0)
     {
         BulkPlan bp;
         // (shorter rows stay with k_rowx: tiles of a few KB and walks over a
@@ -520,7 +522,7 @@ struct Pipe {
         const int LP = lpr * epl;
         const int LSW = (LP + 31) & ~31;
         const int nt = 256;
-        const int nb_env = env_int("EXSUM_ROWX_NBUF", 0);
+        const int nb_env = nbuf_force ? nbuf_force : env_int("EXSUM_ROWX_NBUF", 0);
         const int rows_pass = (nt / 32) * (32 / lpr);
         const int G = rowbulk_segs((int)L, kmax, nt);
         // block-aligned walk when the tile can be a multiple of the segments
@@ -534,7 +536,7 @@ struct Pipe {
                 step = rows_pass;
             }
         }
-        const int tr_env = env_int("EXSUM_ROWX_TR", 0);
+        const int tr_env = tr_force ? tr_force : env_int("EXSUM_ROWX_TR", 0);
         auto sm = [&](int tr, int nb) {
             const bool al = kfull && (tr / G) % kk == 0 && tr % G == 0;
             return rowbulk_smem(tr, kk, al, (int)L, LSW, nb);
