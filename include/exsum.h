@@ -183,6 +183,42 @@ int exsum_excluded_noalloc(const void *in, void *out, int d, const int64_t *shap
 int exsum_release_cached_workspace(void);
 
 /* ---------------------------------------------------------------------------
+ * The paper's comparison methods on the GPU (baselines for box-complement;
+ * same arguments, ownership and stream semantics as exsum_excluded).
+ * ------------------------------------------------------------------------- */
+
+/*
+ * Summed-area table (Sec. 1, SAT / SATC): the inclusive prefix along every
+ * dimension, then at every x the alternating sum of the table at the 2^d
+ * corners of the box (inclusion-exclusion) -- the included sum, or with
+ * excluded != 0 the weak excluded sum (total minus the included sum).
+ * Integer + only (it needs an inverse), wrapping modulo 2^32 or 2^64, so the
+ * result equals the strong excluded sum bit for bit; other dtypes give
+ * EXSUM_EUNSUPPORTED.  Workspace: N elements of the dtype (cached, as for
+ * exsum_excluded).
+ */
+int exsum_sat(const void *in, void *out, int d, const int64_t *shape, const int64_t *k, int excluded, int dtype,
+              void *stream);
+
+/*
+ * Corners (App. A): the 2^d tensors T_b of (+) over the orthant below or
+ * above each point in every dimension (b in {prefix, suffix}^d, from
+ * 2^(d+1) - 2 inclusive scans), then out[x] = (+) of one entry of each,
+ * at the box's corners shifted so that the 2^d orthants tile the complement
+ * of the box exactly -- the strong excluded sum, for + and max, d = 2 or 3
+ * (EXSUM_EUNSUPPORTED otherwise).  Workspace: 2^(d+1) - 2 tensors of the
+ * carry type (fp32 +: compensated pairs, 8 bytes).
+ */
+int exsum_corners(const void *in, void *out, int d, const int64_t *shape, const int64_t *k, int op, int dtype,
+                  void *stream);
+
+/* The region of dimension `dim` that corner `corner` of exsum_corners takes
+ * for d = 2 or 3: 0 below x, 1 below x + k, 2 from x on, 3 from x + k on
+ * (-1 for arguments out of range).  Host only; lets a test check that the
+ * regions tile the complement of the box. */
+int exsum_corner_region(int d, int corner, int dim);
+
+/* ---------------------------------------------------------------------------
  * Batches of uneven tensors.  Not in the paper; it batches many independent
  * excluded sums (Sec. 5) so that they fill the GPU together.
  * ------------------------------------------------------------------------- */

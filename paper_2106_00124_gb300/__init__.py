@@ -107,6 +107,11 @@ _SIG = {
     "exsum_batch_info": ([_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                           ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_int64)],
                          ctypes.c_int),
+    "exsum_sat": ([_P, _P, ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                   ctypes.c_int, ctypes.c_int, _P], ctypes.c_int),
+    "exsum_corners": ([_P, _P, ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                       ctypes.c_int, ctypes.c_int, _P], ctypes.c_int),
+    "exsum_corner_region": ([ctypes.c_int, ctypes.c_int, ctypes.c_int], ctypes.c_int),
     "exsum_batch_schedule": ([_P] + [ctypes.POINTER(ctypes.c_int)] * 7, ctypes.c_int),
     "exsum_batch_destroy": ([_P], None),
     "exsum_server_create": ([ctypes.c_size_t, ctypes.c_int], _P),
@@ -295,6 +300,18 @@ def exsum_batch_info(plan):
     return rc, lanes.value, order.value, ws.value, ker.value
 
 
+def exsum_sat(in_ptr, out_ptr, d, shape, k, excluded, dtype, stream=0):
+    return _load().exsum_sat(in_ptr, out_ptr, d, _arr(shape), _arr(k), int(excluded), dtype, stream or None)
+
+
+def exsum_corners(in_ptr, out_ptr, d, shape, k, op, dtype, stream=0):
+    return _load().exsum_corners(in_ptr, out_ptr, d, _arr(shape), _arr(k), op, dtype, stream or None)
+
+
+def exsum_corner_region(d, corner, dim):
+    return _load().exsum_corner_region(d, corner, dim)
+
+
 def exsum_batch_schedule(plan):
     """(status, mode, level_tensors, lc, interleave, tiles_per_vb, tall, persist); mode 0 lanes, 1 levels."""
     v = [ctypes.c_int() for _ in range(7)]
@@ -406,3 +423,18 @@ def excluded_weak(x, k, out=None):
     CUDA tensor, operator +."""
     return _torch_call(lambda i, o, d, sh, kk, op, dt, st: exsum_excluded_weak(i, o, d, sh, kk, dt, st),
                        x, k, "add", out, "exsum_excluded_weak")
+
+
+def sat(x, k, excluded=True, out=None):
+    """Box sums of an integer CUDA tensor through a summed-area table (the
+    paper's SAT / SATC comparator): the weak excluded sum, or the included
+    sum with excluded=False."""
+    def fn(i, o, d, sh, kk, op, dt, st):
+        return exsum_sat(i, o, d, sh, kk, excluded, dt, st)
+    return _torch_call(fn, x, k, "add", out, "exsum_sat")
+
+
+def corners(x, k, op="add", out=None):
+    """Strong excluded sums of a d = 2 or 3 CUDA tensor by the corners
+    algorithm (the paper's comparator, App. A)."""
+    return _torch_call(exsum_corners, x, k, op, out, "exsum_corners")

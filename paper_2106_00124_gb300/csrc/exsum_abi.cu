@@ -523,6 +523,14 @@ int exsum_graph_exec_destroy(void *exec)
 }  // extern "C"
 
 namespace exsum {
+// For the other translation units (exsum_cmp.cu): argument checks and the
+// cached per-stream workspace.
+int validate_args(int d, const int64_t *shape, const int64_t *k, int op, int dtype)
+{
+    return validate(d, shape, k, op, dtype);
+}
+int cached_ws(void *stream, size_t need, void **ws, size_t *bytes) { return cached_workspace(stream, need, ws, bytes); }
+
 // exsum_excluded_ws without the side stream: everything on `stream`, no
 // stream or event is ever created (used by the allocation-free entry point).
 int excluded_ws_serial(const void *in, void *out, int d, const int64_t *shape, const int64_t *k,

@@ -43,7 +43,10 @@ using Lt = M::loc_t;
 using C = M::car_t;
 using AccC = MC::acc_t;
 
-constexpr int kThreads[NLV] = {128, 128, 128, 128, 256, 256, 256, 256, 256, 256};
+constexpr int kThreads[NLV] = {128, 128, 128, 128, 256, 128, 256, 256, 256, 256};
+// the lower problem: one warp per plane, four per block, each holding 2 n_2
+// accumulators in shared memory (at most 64 KB a block)
+constexpr int LV_E2_N2 = 1024;
 
 int64_t cdiv64(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
@@ -83,10 +86,11 @@ bool level_accepts(const exsum_desc &d, int sms)
     const int64_t *n = d.shape, *k = d.k;
     if (d.d == 2) {
         // the small two-dimensional path of the single-tensor schedule
-        return n[1] <= 4096 && k[0] <= 64 && N <= (1 << 20) && k[0] * N <= (1 << 24);
+        return n[1] <= LV_E2_N2 && n[0] <= PM::SMALL2D_N1 && k[0] <= 64 && N <= (1 << 20) &&
+               k[0] * N <= (1 << 24);
     }
     if (d.d != 3) return false;
-    if (n[1] > 4096 || k[0] > 64 || k[0] > 32 || n[0] >= (1ll << 31) || N >= (1ll << 40)) return false;
+    if (n[1] > LV_E2_N2 || k[0] > 32 || n[0] > PM::SMALL2D_N1 || N >= (1ll << 40)) return false;
     const auto rp = PM::row_plan(3, n, k, sms);
     if (!rp.ok) return false;
     if (!rp.fuse && k[1] > 32) return false;
@@ -211,10 +215,10 @@ void plan_tensor(const exsum_desc &d, const LevelTune &tune, int sms, Carver &cv
         e.n2 = (int)n[1];
         e.k = (int)k[0];
         e.k2 = (int)k[1];
-        e.vgrid = n[0];
-        e.count = n[0];
+        e.vgrid = cdiv64(n[0], 4);
+        e.count = e.vgrid;
         pl.items[LV3].push_back(e);
-        pl.smem[LV3] = std::max(pl.smem[LV3], 2 * (size_t)n[1] * sizeof(AccC));
+        pl.smem[LV3] = std::max(pl.smem[LV3], 2 * 4 * (size_t)n[1] * sizeof(AccC));
         return;
     }
     const int64_t n0 = n[0], n1 = n[1], L = n[2], rows = n0 * n1, N = rows * L;
@@ -286,10 +290,10 @@ void plan_tensor(const exsum_desc &d, const LevelTune &tune, int sms, Carver &cv
         e.n2 = (int)n1;
         e.k = (int)k[0];
         e.k2 = (int)k[1];
-        e.vgrid = n0;
-        e.count = n0;
+        e.vgrid = cdiv64(n0, 4);
+        e.count = e.vgrid;
         pl.items[LV3].push_back(e);
-        pl.smem[LV3] = std::max(pl.smem[LV3], 2 * (size_t)n1 * sizeof(AccC));
+        pl.smem[LV3] = std::max(pl.smem[LV3], 2 * 4 * (size_t)n1 * sizeof(AccC));
     }
     // level 4: the final pass
     const Lt *cur = P >= 1 ? B : static_cast<const Lt *>(X);

@@ -303,6 +303,119 @@ __device__ __forceinline__ void k_exc2d_body(const SR *__restrict__ R, const typ
     }
 }
 
+// ---------------------------------------------------------------------------
+// The same excluded sums, one WARP per plane x1 (blockDim / 32 planes per
+// block, no block barrier), for n2 small enough that each warp keeps H1 and
+// its suffixes in shared memory (dynamic: 2 * n2 accumulators per warp):
+//   T2 over the plane totals (lanes stride over y, then a reduction tree
+//   whose result lane 0 broadcasts: a fixed order);
+//   backwards over chunks of 32 columns: H1 (k1 plane loads per column,
+//   coalesced across the lanes) and its inclusive suffixes (warp scan of the
+//   chunk, then the carry from the chunk after it);
+//   forwards: the exclusive prefixes the same way, and every output
+//   T2 (+) prefix before x2 (+) suffix from x2 + k2.
+// ---------------------------------------------------------------------------
+template <class M>
+__device__ __forceinline__ typename M::acc_t warp_sum0(typename M::acc_t v)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        const typename M::acc_t w = shfl_down(v, d);
+        if (lane + d < 32) v = M::op(v, w);
+    }
+    return shfl_idx(v, 0);
+}
+
+template <class M, class SR = typename M::car_t, class ST = typename M::car_t>
+__device__ __forceinline__ void k_exc2d_w_body(const SR *__restrict__ R, const typename M::car_t *__restrict__ R2,
+                                               ST *__restrict__ T, int n1, int n2, int k1, int k2, int64_t vbid,
+                                               int64_t vgrid)
+{
+    using A = typename M::acc_t;
+    extern __shared__ __align__(16) unsigned char e2w_smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    A *hv = reinterpret_cast<A *>(e2w_smem) + (int64_t)warp * 2 * n2;
+    A *sf = hv + n2;
+    pdl_trigger();
+    pdl_wait();   // R and R2 come from the kernel before
+    const int64_t x1l = vbid * nw + warp;
+    if (x1l >= n1) return;   // a whole warp; nothing below waits for the block
+    const int x1 = (int)x1l;
+    A t2 = M::id();
+    for (int y = lane; y < n1; y += 32)
+        if (y < x1 || y >= x1 + k1) t2 = M::op(t2, M::get(R2[y]));
+    t2 = warp_sum0<M>(t2);
+    const int kw = min(k1, n1 - x1);
+    const SR *row = R + (int64_t)x1 * n2;
+    const int nc = (n2 + 31) >> 5;
+    A carry = M::id();
+    for (int c = nc - 1; c >= 0; --c) {
+        const int x2 = (c << 5) + lane;
+        A h = M::id();
+        if (x2 < n2) {
+            const SR *col = row + x2;
+            h = M::get(col[0]);
+            for (int i0 = 1; i0 < kw; i0 += 8) {
+                SR v[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+                    if (i0 + i < kw) v[i] = col[(int64_t)(i0 + i) * n2];
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+                    if (i0 + i < kw) h = M::op(h, M::get(v[i]));
+            }
+            hv[x2] = h;
+        }
+        A s = h;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const A w = shfl_down(s, d);
+            if (lane + d < 32) s = M::op(s, w);
+        }
+        s = M::op(s, carry);
+        if (x2 < n2) sf[x2] = s;
+        carry = shfl_idx(s, 0);
+    }
+    __syncwarp();
+    A run = M::id();
+    for (int c = 0; c < nc; ++c) {
+        const int x2 = (c << 5) + lane;
+        const A h = x2 < n2 ? hv[x2] : M::id();
+        A p = h;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const A w = shfl_up(p, d);
+            if (lane >= d) p = M::op(w, p);
+        }
+        A ex = shfl_up(p, 1);
+        if (lane == 0) ex = M::id();
+        ex = M::op(run, ex);
+        run = M::op(run, shfl_idx(p, 31));
+        if (x2 < n2) {
+            const A sx = x2 + k2 < n2 ? sf[x2 + k2] : M::id();
+            T[(int64_t)x1 * n2 + x2] = M::template put<ST>(M::op(t2, M::op(ex, sx)));
+        }
+    }
+}
+
+template <class M, class SR = typename M::car_t, class ST = typename M::car_t>
+__global__ void __launch_bounds__(256)
+k_exc2d_w(const SR *__restrict__ R, const typename M::car_t *__restrict__ R2, ST *__restrict__ T, int n1, int n2,
+          int k1, int k2)
+{
+    k_exc2d_w_body<M, SR, ST>(R, R2, T, n1, n2, k1, k2, blockIdx.x, gridDim.x);
+}
+
+// Warps per block of k_exc2d_w for rows of n2 accumulators of `acc` bytes:
+// 2 n2 accumulators per warp in at most 64 KB, at most 8 warps.
+__host__ __device__ inline int exc2d_w_warps(int n2, int acc)
+{
+    int w = 8;
+    while (w > 1 && (size_t)2 * n2 * acc * w > 64 * 1024) w >>= 1;
+    return w;
+}
+
 template <class M, class SR = typename M::car_t, class ST = typename M::car_t>
 __global__ void __launch_bounds__(256)
 k_exc2d(const SR *__restrict__ R, const typename M::car_t *__restrict__ R2, ST *__restrict__ T, int n1,

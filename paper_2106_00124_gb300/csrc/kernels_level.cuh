@@ -182,10 +182,10 @@ kl_plane(LvList ls)
     });
 }
 
-// ---- the two-dimensional lower problem (256 threads): one virtual block per x1 ----
+// ---- the two-dimensional lower problem (128 threads): one warp per x1 ----------
 // d = 3: T = excluded(R) in the carry type; d = 2: the output itself.
 template <class M, bool PERSIST>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(128)
 kl_exc2d(LvList ls)
 {
     using IN = typename M::in_t;
@@ -194,11 +194,11 @@ kl_exc2d(LvList ls)
     lv_pull<PERSIST>(ls, [&](const LvItem &w, int64_t vb) {
         const C *R2 = static_cast<const C *>(w.t);
         if (w.kind == LV_E2_IN)
-            k_exc2d_body<M, IN, OUT>(static_cast<const IN *>(w.src), R2, static_cast<OUT *>(w.dst), w.n, w.n2,
-                                     w.k, w.k2, vb, w.vgrid);
+            k_exc2d_w_body<M, IN, OUT>(static_cast<const IN *>(w.src), R2, static_cast<OUT *>(w.dst), w.n, w.n2,
+                                       w.k, w.k2, vb, w.vgrid);
         else
-            k_exc2d_body<M, C, C>(static_cast<const C *>(w.src), R2, static_cast<C *>(w.dst), w.n, w.n2, w.k,
-                                  w.k2, vb, w.vgrid);
+            k_exc2d_w_body<M, C, C>(static_cast<const C *>(w.src), R2, static_cast<C *>(w.dst), w.n, w.n2, w.k,
+                                    w.k2, vb, w.vgrid);
         return true;
     });
 }

@@ -337,6 +337,21 @@ __device__ __forceinline__ f2 shfl_down(f2 v, int dl)
     return r;
 }
 
+// The value of lane `src`.
+__device__ __forceinline__ int32_t shfl_idx(int32_t v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+__device__ __forceinline__ int64_t shfl_idx(int64_t v, int src)
+{
+    return (int64_t)__shfl_sync(0xffffffffu, (long long)v, src);
+}
+__device__ __forceinline__ float shfl_idx(float v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+__device__ __forceinline__ f2 shfl_idx(f2 v, int src)
+{
+    f2 r;
+    r.hi = __shfl_sync(0xffffffffu, v.hi, src);
+    r.lo = __shfl_sync(0xffffffffu, v.lo, src);
+    return r;
+}
+
 // Segmented variants: lanes exchange only within aligned groups of `w` lanes.
 __device__ __forceinline__ int32_t shfl_up_w(int32_t v, int dl, int w) { return __shfl_up_sync(0xffffffffu, v, dl, w); }
 __device__ __forceinline__ int64_t shfl_up_w(int64_t v, int dl, int w)

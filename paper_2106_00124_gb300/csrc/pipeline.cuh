@@ -144,6 +144,9 @@ struct Pipe {
     using CAR = typename M::car_t;
 
     static constexpr int EXL = 32;            // segment length of the dimension-1 step
+    // the two-kernel lower problem combines all n_1 plane totals for each
+    // plane: at most this many planes
+    static constexpr int64_t SMALL2D_N1 = 16384;
     static constexpr int INC_THREADS = 128;
     static constexpr size_t SLOT_SMEM_MAX = 96 * 1024;
 
@@ -728,16 +731,42 @@ struct Pipe {
         else
             k_plane_totals<MC, SP><<<(unsigned)n1, 256, 0, cx.stream>>>(P, H, Rw, R2, (int)n2);
         cx.check_launch();
-        const size_t smem = 2 * (size_t)n2 * sizeof(typename MC::acc_t);
-        auto kern = k_exc2d<MC>;
-        if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cx.before(TAG_EXC2D, n1 * n2);
-        if (pdl)
-            launch_pdl(kern, (unsigned)n1, 256, smem, cx.stream, R, R2, T, (int)n1, (int)n2, (int)k1, (int)k2);
-        else
-            kern<<<(unsigned)n1, 256, smem, cx.stream>>>(R, R2, T, (int)n1, (int)n2, (int)k1, (int)k2);
-        cx.check_launch();
+        exc2d_launch<CAR, CAR>(cx, R, R2, T, n1, n2, k1, k2, pdl);
         cx.level--;
+    }
+
+    // Excluded sums of the n1 x n2 array R with box (k1, k2) from its plane
+    // totals R2: one warp per plane (k_exc2d_w) when there are planes enough
+    // to fill the GPU that way, else one block per plane (k_exc2d: a few
+    // planes each get a whole block's parallelism).
+    template <class SR, class ST>
+    static void exc2d_launch(Ctx &cx, const SR *R, const CAR *R2, ST *T, int64_t n1, int64_t n2, int64_t k1,
+                             int64_t k2, bool pdl)
+    {
+        using Acc = typename MC::acc_t;
+        if (n1 < 8 * cx.sms) {
+            const size_t smem = 2 * (size_t)n2 * sizeof(Acc);
+            auto kern = k_exc2d<MC, SR, ST>;
+            if (smem > 48 * 1024)
+                cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (pdl)
+                launch_pdl(kern, (unsigned)n1, 256, smem, cx.stream, R, R2, T, (int)n1, (int)n2, (int)k1, (int)k2);
+            else
+                kern<<<(unsigned)n1, 256, smem, cx.stream>>>(R, R2, T, (int)n1, (int)n2, (int)k1, (int)k2);
+            cx.check_launch();
+            return;
+        }
+        const int wpb = exc2d_w_warps((int)n2, (int)sizeof(Acc));
+        const size_t smem = 2 * (size_t)wpb * n2 * sizeof(Acc);
+        auto kern = k_exc2d_w<MC, SR, ST>;
+        if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        const unsigned grid = (unsigned)cdiv(n1, wpb);
+        if (pdl)
+            launch_pdl(kern, grid, 32 * wpb, smem, cx.stream, R, R2, T, (int)n1, (int)n2, (int)k1, (int)k2);
+        else
+            kern<<<grid, 32 * wpb, smem, cx.stream>>>(R, R2, T, (int)n1, (int)n2, (int)k1, (int)k2);
+        cx.check_launch();
     }
 
     template <class SIn, class SOut>
@@ -763,7 +792,7 @@ struct Pipe {
         // first pass is the 16-byte strided pass along dimension 1 over rows
         // of whole 128-element groups, it also leaves partial row totals, and
         // X is read once instead of twice (kernels_fold.cuh).
-        const bool lower2 = d == 3 && n[1] <= 4096 && k[0] <= 64 && n[0] < (1ll << 31);
+        const bool lower2 = d == 3 && n[1] <= 4096 && k[0] <= 64 && n[0] <= SMALL2D_N1;
         bool fold = false;
         if constexpr (sizeof(L_) == 4 && sizeof(SOut) == 4)
             fold = lower2 && P > 0 && dims[0] == 0 && (L % 128) == 0 && k[0] <= 8 &&
@@ -887,20 +916,17 @@ struct Pipe {
         // A small two-dimensional tensor: plane totals, then one block per
         // row of the output (kernels_fold.cuh), the whole sum in the long
         // accumulator -- two short kernels instead of a chain of passes.
-        if (d == 2 && n[1] <= 4096 && k[0] <= 64 && N <= (1 << 20) && k[0] * N <= (1 << 24) &&
-            env_int("EXSUM_SMALL2D", 1) != 0) {
+        // (every plane combines all plane totals: n_1 is bounded so that
+        // this stays far below the tensor's own cost)
+        if (d == 2 && n[1] <= 4096 && n[0] <= SMALL2D_N1 && k[0] <= 64 && N <= (1 << 20) &&
+            k[0] * N <= (1 << 24) && env_int("EXSUM_SMALL2D", 1) != 0) {
             CAR *R2 = cx.take<CAR>(n[0]);
             if (cx.dry || !cx.ok()) return;
             cx.before(TAG_PLANE, N);
             k_plane_totals<MC, SIn><<<(unsigned)n[0], 256, 0, cx.stream>>>(X, 1, nullptr, R2, (int)n[1]);
             cx.check_launch();
-            const size_t smem = 2 * (size_t)n[1] * sizeof(typename MC::acc_t);
-            auto kern = k_exc2d<MC, SIn, SOut>;
-            if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             cx.before(TAG_EXC2D, N);
-            launch_pdl(kern, (unsigned)n[0], 256, smem, cx.stream, X, (const CAR *)R2, out, (int)n[0], (int)n[1],
-                       (int)k[0], (int)k[1]);
-            cx.check_launch();
+            exc2d_launch<SIn, SOut>(cx, X, R2, out, n[0], n[1], k[0], k[1], true);
             return;
         }
         const RowPlan rp = row_plan(d, n, k, cx.sms);

@@ -144,3 +144,27 @@ def test_parity_many_tiles_per_block(shape, k, dtype, op):
     got = gpu_sum("excluded", to_device(dev, dtype), k, op)
     check(got, oracle_sum("excluded", vals, k, op), dtype, op,
           "many tiles %s %s %s k=%s" % (dtype, op, shape, k))
+
+
+# Lower problems of many planes: the two-dimensional excluded sum runs one
+# warp per plane (d = 2 tensors of >= 1216 rows, and d = 3 tensors whose
+# first dimension is that long), including planes of one column, boxes
+# covering the whole plane and windows reaching past the last plane.
+MANY_PLANES = [
+    ((1500, 37), (5, 7)),
+    ((4000, 60), (64, 3)),
+    ((1300, 700), (16, 600)),
+    ((2048, 1), (9, 1)),
+    ((1300, 20, 16), (10, 3, 4)),
+    ((1250, 9, 33), (64, 9, 2)),
+]
+
+
+@pytest.mark.parametrize("dtype,op", [("f32", "add"), ("i64", "max"), ("i32", "add"), ("bf16", "add")])
+@pytest.mark.parametrize("shape,k", MANY_PLANES, ids=[str(c[0]) + "k" + str(c[1]) for c in MANY_PLANES])
+def test_parity_many_planes(shape, k, dtype, op):
+    seed = zlib.crc32(repr((shape, k, dtype, op, "planes")).encode()) & 0xFFFFFF
+    dev, vals = seeded(shape, dtype, seed, op)
+    got = gpu_sum("excluded", to_device(dev, dtype), k, op)
+    check(got, oracle_sum("excluded", vals, k, op), dtype, op,
+          "many planes %s %s %s k=%s" % (dtype, op, shape, k))
