@@ -57,10 +57,12 @@ def parse_args(argv=None):
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-extras", action="store_true",
                    help="skip the compact batched and served figures of the default line")
-    p.add_argument("--mode", choices=["single", "batched", "served"], default="single",
+    p.add_argument("--mode", choices=["single", "batched", "served", "comparators"], default="single",
                    help="single: the default step; batched: 512 uneven tensors as one graph "
                         "launch vs plain per-tensor launches; served: a Poisson request stream "
-                        "at three offered loads (p50/p99) vs one-at-a-time plain launches")
+                        "at three offered loads (p50/p99) vs one-at-a-time plain launches; "
+                        "comparators: SAT/SATC, BDBSC and corners against box-complement over d, "
+                        "and operator applications per element with a slowed operator")
     p.add_argument("--requests", type=int, default=20000)
     p.add_argument("--profile-once", action="store_true",
                    help="run the workload's excluded sum twice without graphs or timing "
@@ -430,8 +432,8 @@ def run_ours(args):
         except Exception as e:  # no OpenMP-capable compiler on this host
             cpu["all_cores"] = {"unavailable": str(e)[:200]}
 
-    # ---- compact batched and served figures (rank 0, N = 1) -----------------------------------
-    batched = served = None
+    # ---- compact batched, served and comparator figures (rank 0, N = 1) -----------------------------------
+    batched = served = comparators = None
     if rank == 0 and world == 1 and not args.no_extras:
         try:
             batched = batched_bench(64, steps=10, warmup=2, plain_steps=2)
@@ -441,6 +443,10 @@ def run_ours(args):
             served = served_bench(1500)
         except Exception as e:
             served = {"error": str(e)[:300]}
+        try:
+            comparators = comparators_bench(compact=True)
+        except Exception as e:
+            comparators = {"error": str(e)[:300]}
 
     if rank == 0:
         line = {
@@ -462,7 +468,7 @@ def run_ours(args):
                         "ms_per_step": round(warm_ms, 5), "steps": warm_steps,
                         "note": "same graph back to back, no L2 flush between steps"},
             "e2e": e2e, "gpu_launches": launches, "clocks": clk, "cpu_baseline": cpu,
-            "batched": batched, "served": served,
+            "batched": batched, "served": served, "comparators": comparators,
             "accuracy": accuracy,
         }
         print(json.dumps(line), flush=True)
@@ -841,6 +847,93 @@ def served_bench(nreq, slots=8, seed=12):
                    "plain": "the same arrivals, one exsum_excluded call each on one stream"}}
 
 
+def _event_ms(fn, reps):
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def comparators_bench(compact=False, reps=5):
+    """The paper's comparison methods on this GPU (int64 +, seeded uniform
+    [-1000, 1000], k = 8 per dimension, about 2^24 elements per d; d = 1
+    uses k = 64): box-complement (strong excluded sum), BDBSC (weak),
+    SAT with inclusion-exclusion (weak) and corners (strong, d = 2, 3), in
+    Gelem/s; then the operator cost: the slowed int64 + at several extra
+    costs on a 128^3 tensor (k = 4), each method's slope of time against
+    the extra cost over the calibration kernel's slope per application:
+    operator applications per element, weighted by how serial each method's
+    chains of applications are.  Returns the record."""
+    import numpy as np
+    import torch
+
+    import paper_2106_00124_gb300 as ex
+    torch.cuda.set_device(0)
+    sweep = [(3, 256)] if compact else [(1, 1 << 24), (2, 4096), (3, 256), (4, 64), (5, 28), (6, 16)]
+    rows = []
+    g = torch.Generator(device="cuda")
+    for d, side in sweep:
+        sh = [side] * d
+        k = [64] if d == 1 else [8] * d
+        N = int(np.prod(sh))
+        g.manual_seed(1000 + d)
+        x = torch.randint(-1000, 1001, sh, dtype=torch.int64, device="cuda", generator=g)
+        o = torch.empty_like(x)
+        r = {"d": d, "shape": sh, "k": k}
+        for name, fn in (("box_complement", lambda: ex.excluded(x, k, "add", out=o)),
+                         ("bdbsc", lambda: ex.excluded_weak(x, k, out=o)),
+                         ("satc", lambda: ex.sat(x, k, excluded=True, out=o)),
+                         ("corners", (lambda: ex.corners(x, k, "add", out=o)) if d in (2, 3) else None)):
+            if fn is None:
+                continue
+            ms = _event_ms(fn, reps)
+            r[name] = {"ms": round(ms, 4), "gelem_s": round(N / (ms * 1e-3) / 1e9, 2)}
+        rows.append(r)
+        del x, o
+    # operator cost
+    sh, k = [128, 128, 128], [4, 4, 4]
+    N = int(np.prod(sh))
+    g.manual_seed(77)
+    x = torch.randint(-1000, 1001, sh, dtype=torch.int64, device="cuda", generator=g)
+    o = torch.empty_like(x)
+    sp = torch.cuda.current_stream().cuda_stream
+    extras = [0, 64, 256] if compact else [0, 32, 64, 128, 256]
+    methods = {"calibration": ex.SLOW_CALIBRATE, "box_complement": ex.SLOW_BOX_COMPLEMENT,
+               "bdbs": ex.SLOW_BDBS, "corners": ex.SLOW_CORNERS}
+    times = {m: [] for m in methods}
+    try:
+        for e in extras:
+            assert ex.exsum_slow_extra(e) == 0
+            for m, code in methods.items():
+                def run(code=code):
+                    rc = ex.exsum_slow_run(x.data_ptr(), o.data_ptr(), 3, sh, k, code, sp)
+                    assert rc == 0, ex.strerror(rc)
+                times[m].append(_event_ms(run, 2))
+    finally:
+        ex.exsum_slow_extra(0)
+    slope = {m: float(np.polyfit(extras, t, 1)[0]) for m, t in times.items()}
+    per_app = slope["calibration"] / ex.SLOW_CALIBRATE_REPS
+    ops = {m: round(slope[m] / per_app, 2) for m in methods if m != "calibration"}
+    return {"metric": "comparators: Gelem/s per method and d; operator applications per element",
+            "dtype": "i64", "op": "add", "data": "synthetic (seeded, on device)", "sweep": rows,
+            "operator_cost": {"shape": sh, "k": k, "extra_costs": extras,
+                              "ms": {m: [round(t, 4) for t in v] for m, v in times.items()},
+                              "effective_applications_per_element": ops,
+                              "note": "time slope per unit of operator cost over that of one fully parallel "
+                                      "application per element: operator applications per element, weighted "
+                                      "by how serial their chains are (a thread walking a line pays latency)"}}
+
+
+def run_comparators(args):
+    print(json.dumps(comparators_bench()), flush=True)
+
+
 def run_served(args):
     """The served workload at its full request count."""
     import torch
@@ -855,6 +948,9 @@ def main(argv=None):
         return
     if args.mode == "served":
         run_served(args)
+        return
+    if args.mode == "comparators":
+        run_comparators(args)
         return
     if args.profile_once:
         run_profile_once(args)

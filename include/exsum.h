@@ -218,6 +218,24 @@ int exsum_corners(const void *in, void *out, int d, const int64_t *shape, const 
  * regions tile the complement of the box. */
 int exsum_corner_region(int d, int corner, int dim);
 
+/*
+ * Operator-cost experiment (the paper's slowed operator, Sec. 6): int64 +
+ * whose every application also runs `extra` dependent steps that leave its
+ * value unchanged (exsum_slow_extra sets it for the device, >= 0), through
+ * box-complement's
+ * row schedule (strong excluded sum), BDBS (included sum), corners (d = 2,
+ * 3) or a calibration kernel applying the operator
+ * EXSUM_SLOW_CALIBRATE_REPS times per element.  The slope of time against
+ * `extra`, over the calibration's slope per application, is the number of
+ * operator applications per element of a method.  int64 input and output,
+ * arguments as for exsum_excluded.
+ */
+enum { EXSUM_SLOW_BOX_COMPLEMENT = 0, EXSUM_SLOW_BDBS = 1, EXSUM_SLOW_CORNERS = 2, EXSUM_SLOW_CALIBRATE = 3 };
+#define EXSUM_SLOW_CALIBRATE_REPS 16
+int exsum_slow_extra(int extra);
+int exsum_slow_run(const void *in, void *out, int d, const int64_t *shape, const int64_t *k, int method,
+                   void *stream);
+
 /* ---------------------------------------------------------------------------
  * Batches of uneven tensors.  Not in the paper; it batches many independent
  * excluded sums (Sec. 5) so that they fill the GPU together.

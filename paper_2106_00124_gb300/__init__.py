@@ -112,6 +112,9 @@ _SIG = {
     "exsum_corners": ([_P, _P, ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                        ctypes.c_int, ctypes.c_int, _P], ctypes.c_int),
     "exsum_corner_region": ([ctypes.c_int, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+    "exsum_slow_extra": ([ctypes.c_int], ctypes.c_int),
+    "exsum_slow_run": ([_P, _P, ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                        ctypes.c_int, _P], ctypes.c_int),
     "exsum_batch_schedule": ([_P] + [ctypes.POINTER(ctypes.c_int)] * 7, ctypes.c_int),
     "exsum_batch_destroy": ([_P], None),
     "exsum_server_create": ([ctypes.c_size_t, ctypes.c_int], _P),
@@ -310,6 +313,18 @@ def exsum_corners(in_ptr, out_ptr, d, shape, k, op, dtype, stream=0):
 
 def exsum_corner_region(d, corner, dim):
     return _load().exsum_corner_region(d, corner, dim)
+
+
+SLOW_BOX_COMPLEMENT, SLOW_BDBS, SLOW_CORNERS, SLOW_CALIBRATE = 0, 1, 2, 3
+SLOW_CALIBRATE_REPS = 16
+
+
+def exsum_slow_extra(extra):
+    return _load().exsum_slow_extra(int(extra))
+
+
+def exsum_slow_run(in_ptr, out_ptr, d, shape, k, method, stream=0):
+    return _load().exsum_slow_run(in_ptr, out_ptr, d, _arr(shape), _arr(k), int(method), stream or None)
 
 
 def exsum_batch_schedule(plan):

@@ -84,6 +84,101 @@ k_scan_rows(const SR *in, SW *out, int64_t rows, int64_t L)
     }
 }
 
+// Long lines in few of them: each line is cut into nseg segments of G
+// elements, scanned independently (k_scan_seg: one thread per (line,
+// segment) for I > 1, one warp for I == 1), then the carry of every segment
+// -- the (+) of the totals of the segments before it (after it, for a
+// suffix) -- is formed per line in segment order (k_seg_carry) and combined
+// into the segment's elements (k_seg_apply).
+template <class M, class SR, class SW, bool SUF>
+__global__ void __launch_bounds__(256)
+k_scan_seg(const SR *in, SW *out, int64_t O, int64_t n, int64_t I, int64_t G, int64_t nseg)
+{
+    using A = typename M::acc_t;
+    if (I == 1) {
+        const int lane = threadIdx.x & 31;
+        const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+        if (w >= O * nseg) return;   // whole warps
+        const int64_t o = w / nseg, sg = w - o * nseg;
+        const int64_t a = sg * G, len = min(G, n - a);
+        const SR *src = in + o * n + a;
+        SW *dst = out + o * n + a;
+        A carry = M::id();
+        for (int64_t c0 = 0; c0 < len; c0 += 32) {
+            const int64_t t = c0 + lane;
+            const int64_t x = SUF ? len - 1 - t : t;
+            A v = t < len ? M::get(src[x]) : M::id();
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const A u = shfl_up(v, d);
+                if (lane >= d) v = M::op(u, v);
+            }
+            v = M::op(carry, v);
+            if (t < len) dst[x] = M::template put<SW>(v);
+            carry = shfl_idx(v, 31);
+        }
+        return;
+    }
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= O * nseg * I) return;
+    const int64_t i = gid % I, r = gid / I, sg = r % nseg, o = r / nseg;
+    const int64_t a = sg * G, len = min(G, n - a);
+    const SR *src = in + (o * n + a) * I + i;
+    SW *dst = out + (o * n + a) * I + i;
+    A acc = M::id();
+    for (int64_t t0 = 0; t0 < len; t0 += 8) {
+        SR v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int64_t t = t0 + u;
+            if (t < len) v[u] = src[(SUF ? len - 1 - t : t) * I];
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int64_t t = t0 + u;
+            if (t < len) {
+                acc = M::op(acc, M::get(v[u]));
+                dst[(SUF ? len - 1 - t : t) * I] = M::template put<SW>(acc);
+            }
+        }
+    }
+}
+
+// Carries: Cy[(o * nseg + s) * I + i] = (+) of the totals of the segments
+// before s (SUF: after s) of line (o, i); a segment's total is its scan at
+// its last (SUF: first) element.
+template <class M, class SW, bool SUF>
+__global__ void __launch_bounds__(256)
+k_seg_carry(const SW *__restrict__ out, SW *__restrict__ Cy, int64_t O, int64_t n, int64_t I, int64_t G,
+            int64_t nseg)
+{
+    using A = typename M::acc_t;
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= O * I) return;
+    const int64_t o = gid / I, i = gid - o * I;
+    A run = M::id();
+    for (int64_t t = 0; t < nseg; ++t) {
+        const int64_t sg = SUF ? nseg - 1 - t : t;
+        Cy[(o * nseg + sg) * I + i] = M::template put<SW>(run);
+        const int64_t a = sg * G, len = min(G, n - a);
+        const int64_t x = SUF ? a : a + len - 1;
+        run = M::op(run, M::get(out[(o * n + x) * I + i]));
+    }
+}
+
+template <class M, class SW, bool SUF>
+__global__ void __launch_bounds__(256)
+k_seg_apply(SW *__restrict__ out, const SW *__restrict__ Cy, int64_t O, int64_t n, int64_t I, int64_t G,
+            int64_t nseg)
+{
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= O * n * I) return;
+    const int64_t i = gid % I, r = gid / I, x = r % n, o = r / n;
+    const int64_t sg = x / G;
+    if (SUF ? sg == nseg - 1 : sg == 0) return;   // the carry is the identity
+    out[gid] = M::template put<SW>(M::op(M::get(Cy[(o * nseg + sg) * I + i]), M::get(out[gid])));
+}
+
 // Shape, box and row-major strides of a tensor of at most 8 dimensions.
 struct CmpDims {
     int d;

@@ -49,7 +49,9 @@ def test_comparators_reject_without_gpu():
 
 
 SAT_CASES = [((1000,), (37,)), ((37, 41), (5, 40)), ((19, 23, 29), (4, 23, 1)), ((6, 7, 8, 9), (2, 3, 4, 5)),
-             ((256, 256), (16, 16)), ((3, 5, 2, 4, 3), (2, 2, 2, 2, 2))]
+             ((256, 256), (16, 16)), ((3, 5, 2, 4, 3), (2, 2, 2, 2, 2)),
+             # long lines in few of them: segmented scans with carries
+             ((100000,), (777,)), ((4096, 8), (100, 3)), ((3, 20000), (2, 999))]
 
 
 @pytest.mark.gpu
@@ -66,7 +68,9 @@ def test_sat_matches_oracle(shape, k, excluded, dtype):
 
 CORNER_CASES = [((37, 41), (5, 40)), ((256, 256), (16, 16)), ((1, 9), (1, 9)), ((50, 3), (50, 1)),
                 ((19, 23, 29), (4, 23, 1)), ((64, 64, 64), (8, 8, 8)), ((5, 1, 7), (2, 1, 7)),
-                ((30, 31, 33), (30, 5, 2))]
+                ((30, 31, 33), (30, 5, 2)),
+                # segmented scans (few long lines), both directions
+                ((2000, 5), (30, 2)), ((3, 20000), (2, 999)), ((5000, 2, 3), (7, 2, 1))]
 
 
 @pytest.mark.gpu
@@ -80,3 +84,39 @@ def test_corners_match_oracle(shape, k, dtype, op):
     ref = oracle_sum("excluded", vals, k, op)
     check(got, ref.astype(np.float64) if dtype in ("f32", "bf16") else ref, dtype, op,
           "corners %s %s %s k=%s" % (dtype, op, shape, k))
+
+
+def test_slowed_operator_rejects_without_gpu():
+    assert ex.exsum_slow_extra(-1) == ex.EXSUM_EINVAL
+    assert ex.exsum_slow_run(16, 32, 2, [4, 4], [2, 2], 9, 0) == ex.EXSUM_EINVAL
+    assert ex.exsum_slow_run(16, 32, 4, [2, 2, 2, 2], [1, 1, 1, 1], ex.SLOW_CORNERS, 0) == ex.EXSUM_EUNSUPPORTED
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("extra", [0, 3])
+@pytest.mark.parametrize("shape,k", [((37, 41), (5, 40)), ((19, 23, 29), (4, 23, 1)), ((9, 8, 7, 6), (2, 3, 4, 5))])
+def test_slowed_operator_pipelines_match_oracle(shape, k, extra):
+    """The slowed int64 + gives the plain sums: box-complement, BDBS and
+    corners through it match the oracle bit for bit, and the calibration
+    kernel applies the operator the stated number of times."""
+    import torch
+    seed = zlib.crc32(repr((shape, k, "slow")).encode()) & 0xFFFFFF
+    dev, vals = seeded(shape, "i64", seed, "add")
+    x = to_device(dev, "i64")
+    out = torch.empty_like(x)
+    s = torch.cuda.current_stream().cuda_stream
+    assert ex.exsum_slow_extra(extra) == ex.EXSUM_OK
+    try:
+        methods = [(ex.SLOW_BOX_COMPLEMENT, "excluded"), (ex.SLOW_BDBS, "included")]
+        if len(shape) in (2, 3):
+            methods.append((ex.SLOW_CORNERS, "excluded"))
+        for m, kind in methods:
+            out.fill_(5)
+            assert ex.exsum_slow_run(x.data_ptr(), out.data_ptr(), len(shape), shape, k, m, s) == ex.EXSUM_OK
+            torch.cuda.synchronize()
+            check(out.cpu().numpy(), oracle_sum(kind, vals, k, "add"), "i64", "add", "slowed %d %s" % (m, shape))
+        assert ex.exsum_slow_run(x.data_ptr(), out.data_ptr(), len(shape), shape, k, ex.SLOW_CALIBRATE, s) == 0
+        torch.cuda.synchronize()
+        assert torch.equal(out, x * (ex.SLOW_CALIBRATE_REPS + 1))
+    finally:
+        ex.exsum_slow_extra(0)
