@@ -261,7 +261,7 @@ typedef struct exsum_batch exsum_batch;
  *           path, with fp32 +, joins a level set: each pass level of all
  *           those tensors is ONE launch (per register class) whose blocks
  *           take (tensor, pass, tile) items from a device work list -- at
- *           most nine kernels and one memset per replay, whatever the
+ *           most thirteen kernels and one memset per replay, whatever the
  *           batch size.
  *           The other tensors run on one lane beside it;
  *   lanes   the tensors are assigned to `lanes` concurrent streams --
@@ -269,7 +269,9 @@ typedef struct exsum_batch exsum_batch;
  *           (order 1) -- each lane with one workspace sized for its largest
  *           tensor, every tensor with its own chain of kernels.
  * lanes > 0 picks the lanes schedule with that many streams, lanes ==
- * EXSUM_BATCH_LEVELS the level schedule with its default tuning, and
+ * EXSUM_BATCH_LEVELS the level schedule with its default tuning (or the
+ * one the environment variable EXSUM_LEVEL_TUNE gives as
+ * "lc,interleave,tiles_per_vb,tall,persist"; see exsum_batch_schedule), and
  * lanes == 0 autotunes: candidate schedules (levels with several strided
  * chunk lengths, row-total placements, final-pass tiles per block and tile
  * heights; lanes with 1..32 streams and both orders) are captured and their

@@ -439,6 +439,17 @@ int exsum_batch_create(const exsum_desc *descs, int count, int lanes, void *stre
     } else if (lanes == EXSUM_BATCH_LEVELS) {
         sc.mode = 1;
         sc.lanes = 4;
+        // EXSUM_LEVEL_TUNE="lc,interleave,tiles_per_vb,tall,persist" replaces the defaults
+        if (const char *t = getenv("EXSUM_LEVEL_TUNE")) {
+            int v[5];
+            if (sscanf(t, "%d,%d,%d,%d,%d", &v[0], &v[1], &v[2], &v[3], &v[4]) == 5) {
+                sc.tune.lc = v[0];
+                sc.tune.interleave = v[1];
+                sc.tune.tiles_per_vb = v[2];
+                sc.tune.tall = v[3];
+                sc.tune.persist = v[4];
+            }
+        }
     } else {
         const std::string key = signature(descs, count);
         bool found = false;

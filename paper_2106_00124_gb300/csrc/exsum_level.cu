@@ -1,23 +1,28 @@
 // exsum_level.cu -- the level-batched schedule of a batch of excluded sums:
-// every tensor's passes of one level run in one persistent launch
-// (kernels_level.cuh), so a batch of hundreds of tensors takes at most six
-// kernel launches and one memset, whatever its size.
+// every tensor's passes of one level run in one launch per register class
+// over a device work list (kernels_level.cuh), so a batch of hundreds of
+// tensors takes at most thirteen kernel launches (and, for persistent grids,
+// one memset), whatever its size.
 //
 // A tensor joins a level set when its excluded sum takes the row schedule
-// with the two-dimensional lower problem (d = 3, Sec. 4; n_2 <= 4096,
-// k_1 <= 64, rows of 16 .. 1024 elements, boxes of at most 32 along the
+// with the two-dimensional lower problem (d = 3, Sec. 4; n_2 <= 1024,
+// n_1 <= 16384, rows of 16 .. 1024 elements, boxes of at most 32 along the
 // strided passes) or the two short kernels of a small d = 2 tensor, and
 // its operator and type are fp32 + (the type the level kernels are built
 // for).  Its passes are those of the single-tensor path with the same
-// tile plans, so the arithmetic is the same; only the work lists differ:
+// tile plans (the lower problem excepted, see level 2), so the arithmetic is
+// the same up to the order of the lower problem's window sums; only the work
+// lists differ:
 //   level 1   strided BDBS pass along dimension 1 (X -> B) and the row
 //             totals R of X (d = 3);
 //   level 1b  strided pass along dimension 2 (B2 -> B) when the final pass
 //             does not take that window (side branch, beside levels 2, 3);
-//   level 2   plane totals R2 (of R for d = 3, of X for d = 2);
-//   level 3   the lower problem: T = excluded(R) for d = 3, the output
-//             itself for d = 2;
-//   level 4   the final pass (bulk-staged, or k_rowx on a side branch).
+//   level 2   plane totals R2 (of R for d = 3, of X for d = 2), beside the
+//             window sums H1 of R (or X) along dimension 1 by a strided
+//             BDBS pass in the carry type;
+//   level 3   the lower problem from H1 and R2, one warp per plane:
+//             T = excluded(R) for d = 3, the output itself for d = 2;
+//   level 4   the final pass (bulk-staged, or k_rowx on side branches).
 // Each level's items are ordered largest tensor first, so the small ones
 // fill the tail of the launch.
 #include <cuda_runtime.h>
@@ -34,7 +39,7 @@ namespace exsum {
 namespace {
 
 // levels; the strided and k_rowx levels in two register classes each
-enum { LV1 = 0, LV1_C1, LV1B, LV1B_C1, LV2, LV3, LV4A, LV4B, LV4B_C1, LV4B_C2, NLV };
+enum { LV1 = 0, LV1_C1, LV1B, LV1B_C1, LV2, LV2H, LV2H_C1, LV3, LV4A, LV4A_ODD, LV4B, LV4B_C1, LV4B_C2, NLV };
 
 using M = M_F32_ADD;
 using PM = Pipe<M>;
@@ -43,7 +48,7 @@ using Lt = M::loc_t;
 using C = M::car_t;
 using AccC = MC::acc_t;
 
-constexpr int kThreads[NLV] = {128, 128, 128, 128, 256, 128, 256, 256, 256, 256};
+constexpr int kThreads[NLV] = {128, 128, 128, 128, 256, 128, 128, 128, 256, 256, 256, 256, 256};
 // the lower problem: one warp per plane, four per block, each holding 2 n_2
 // accumulators in shared memory (at most 64 KB a block)
 constexpr int LV_E2_N2 = 1024;
@@ -86,7 +91,7 @@ bool level_accepts(const exsum_desc &d, int sms)
     const int64_t *n = d.shape, *k = d.k;
     if (d.d == 2) {
         // the small two-dimensional path of the single-tensor schedule
-        return n[1] <= LV_E2_N2 && n[0] <= PM::SMALL2D_N1 && k[0] <= 64 && N <= (1 << 20) &&
+        return n[1] <= LV_E2_N2 && n[0] <= PM::SMALL2D_N1 && k[0] <= 32 && N <= (1 << 20) &&
                k[0] * N <= (1 << 24);
     }
     if (d.d != 3) return false;
@@ -192,12 +197,36 @@ struct Planned {
     size_t bytes = 0;
 };
 
+// The window sums H1 along x1 (box k1 <= 32) of the lower problem's input
+// (n1 planes of n2): a strided BDBS pass in the carry type, chunks sized as
+// for the single-tensor pass.  Returns its level.
+int h1_item(LvItem &w, const void *src, bool car, C *dst, int64_t n1, int64_t n2, int64_t k1, int sms)
+{
+    int Lc = 128;
+    while (Lc > 2 * k1 && Lc > 16 && cdiv64(n1, Lc) * n2 < (int64_t)sms * 2048) Lc >>= 1;
+    if (Lc > n1) Lc = (int)n1;
+    w = LvItem{};
+    w.kind = (car ? LV_H1C_K4 : LV_H1I_K4) + (k1 <= 4 ? 0 : k1 <= 8 ? 1 : k1 <= 16 ? 2 : 3);
+    w.src = src;
+    w.dst = dst;
+    w.O = 1;
+    w.n = (int)n1;
+    w.I = n2;
+    w.k = (int)k1;
+    w.Lc = Lc;
+    w.nchunks = (int)cdiv64(n1, Lc);
+    w.vgrid = cdiv64((int64_t)w.nchunks * n2, 128);
+    w.count = w.vgrid;
+    return LV2H + lv_class(w.kind);
+}
+
 // Plans one tensor (accepted by level_accepts) into the level lists.
 void plan_tensor(const exsum_desc &d, const LevelTune &tune, int sms, Carver &cv, Planned &pl)
 {
     const int64_t *n = d.shape, *k = d.k;
     if (d.d == 2) {
         C *R2 = cv.take<C>(n[0]);
+        C *H1 = k[0] > 1 ? cv.take<C>(n[0] * n[1]) : nullptr;
         LvItem p{};
         p.kind = LV_PT_IN;
         p.src = d.in;
@@ -209,6 +238,15 @@ void plan_tensor(const exsum_desc &d, const LevelTune &tune, int sms, Carver &cv
         LvItem e{};
         e.kind = LV_E2_IN;
         e.src = d.in;
+        if (H1) {
+            // the window along x1 from a strided pass; the lower kernel reads one plane
+            LvItem h;
+            const int lv = h1_item(h, d.in, false, H1, n[0], n[1], k[0], sms);
+            pl.items[lv].push_back(h);
+            e.kind = LV_E2_CO;
+            e.src = H1;
+        }
+        e.Lc = 1;   // planes combined per window by the lower kernel
         e.t = R2;
         e.dst = d.out;
         e.n = (int)n[0];
@@ -237,6 +275,7 @@ void plan_tensor(const exsum_desc &d, const LevelTune &tune, int sms, Carver &cv
     C *R = cv.take<C>(rows);
     C *T = cv.take<C>(rows);
     C *R2 = cv.take<C>(n0);
+    C *H1 = k[0] > 1 ? cv.take<C>(rows) : nullptr;
     const void *X = d.in;
 
     // level 1: the strided pass along dimension 1 and the row totals
@@ -284,6 +323,13 @@ void plan_tensor(const exsum_desc &d, const LevelTune &tune, int sms, Carver &cv
         LvItem e{};
         e.kind = LV_E2_CAR;
         e.src = R;
+        if (H1) {
+            LvItem h;
+            const int lv = h1_item(h, R, true, H1, n0, n1, k[0], sms);
+            pl.items[lv].push_back(h);
+            e.src = H1;
+        }
+        e.Lc = 1;
         e.t = R2;
         e.dst = T;
         e.n = (int)n0;
@@ -299,7 +345,7 @@ void plan_tensor(const exsum_desc &d, const LevelTune &tune, int sms, Carver &cv
     const Lt *cur = P >= 1 ? B : static_cast<const Lt *>(X);
     const int kk = rp.fuse ? (int)k[1] : 1;
     const int k3 = (int)k[2];
-    const bool bulk_ok = (!cv.base || al16(cur)) && al16(d.out) && (L & 3) == 0 && L >= 128 && L <= 1024 &&
+    const bool bulk_ok = (!cv.base || al16(cur)) && al16(d.out) && L >= 128 && L <= 1024 &&
                          kk <= 32;
     if (bulk_ok) {
         const int kmax = kk <= 1 ? 1 : kk <= 8 ? 8 : 32;
@@ -323,8 +369,9 @@ void plan_tensor(const exsum_desc &d, const LevelTune &tune, int sms, Carver &cv
             const int tpv = tune.tiles_per_vb > 0 ? tune.tiles_per_vb : 2;
             w.vgrid = cdiv64(bp.ntiles, tpv);
             w.count = w.vgrid;
-            pl.items[LV4A].push_back(w);
-            pl.smem[LV4A] = std::max(pl.smem[LV4A], bp.smem);
+            const int lv4a = bp.odd ? LV4A_ODD : LV4A;
+            pl.items[lv4a].push_back(w);
+            pl.smem[lv4a] = std::max(pl.smem[lv4a], bp.smem);
             return;
         }
     }
@@ -368,8 +415,11 @@ KernFn level_kernel_t(int lv)
     case LV1_C1:
     case LV1B_C1: return kl_stage1<M, 1, P>;
     case LV2: return kl_plane<MC, P>;
+    case LV2H: return kl_lower_h1<MC, 0, P>;
+    case LV2H_C1: return kl_lower_h1<MC, 1, P>;
     case LV3: return kl_exc2d<MC, P>;
-    case LV4A: return kl_final_bulk<M, P>;
+    case LV4A: return kl_final_bulk<M, P, false>;
+    case LV4A_ODD: return kl_final_bulk<M, P, true>;
     case LV4B: return kl_final_rowx<M, 0, P>;
     case LV4B_C1: return kl_final_rowx<M, 1, P>;
     default: return kl_final_rowx<M, 2, P>;
@@ -521,11 +571,21 @@ int level_enqueue(LevelSet *ls, cudaStream_t s)
         launch(LV1B_C1, ls->side);
         cudaEventRecord(ls->ev[3], ls->side);
     }
+    // plane totals beside the window sums H1 (both read the lower input)
+    const bool h1 = has(LV2H) || has(LV2H_C1);
+    if (h1) {
+        cudaEventRecord(ls->ev[4], s);
+        cudaStreamWaitEvent(ls->side2, ls->ev[4], 0);
+        launch(LV2H, ls->side2);
+        launch(LV2H_C1, ls->side2);
+        cudaEventRecord(ls->ev[5], ls->side2);
+    }
     launch(LV2, s);
+    if (h1) cudaStreamWaitEvent(s, ls->ev[5], 0);
     launch(LV3, s);
     if (b1) cudaStreamWaitEvent(s, ls->ev[3], 0);
     // the final-pass kernels side by side
-    const int n4 = (int)has(LV4A) + (int)has(LV4B) + (int)has(LV4B_C1) + (int)has(LV4B_C2);
+    const int n4 = (int)has(LV4A) + (int)has(LV4A_ODD) + (int)has(LV4B) + (int)has(LV4B_C1) + (int)has(LV4B_C2);
     if (n4 > 1) {
         cudaEventRecord(ls->ev[4], s);
         cudaStreamWaitEvent(ls->side, ls->ev[4], 0);
@@ -534,12 +594,14 @@ int level_enqueue(LevelSet *ls, cudaStream_t s)
         launch(LV4B_C2, ls->side);
         launch(LV4B_C1, ls->side2);
         launch(LV4A, s);
+        launch(LV4A_ODD, s);
         cudaEventRecord(ls->ev[5], ls->side);
         cudaStreamWaitEvent(s, ls->ev[5], 0);
         cudaEventRecord(ls->ev[1], ls->side2);
         cudaStreamWaitEvent(s, ls->ev[1], 0);
     } else {
         launch(LV4A, s);
+        launch(LV4A_ODD, s);
         launch(LV4B, s);
         launch(LV4B_C1, s);
         launch(LV4B_C2, s);

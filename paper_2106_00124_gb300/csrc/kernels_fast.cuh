@@ -84,6 +84,79 @@ k_inc_strided(const SIn *__restrict__ in, SOut *__restrict__ out, int64_t O, int
 }
 
 // ---------------------------------------------------------------------------
+// BDBS-Along-Dim along a strided dimension for boxes too long to keep a
+// block in registers (k > 32).  The same blocks of k lines and the same
+// combination as bdbs_walk (so the same results), with the block's
+// suffixes kept in the output itself: one thread per (outer, chunk, inner)
+// line chunk of whole blocks; for each block it walks the block backwards,
+// writing the suffixes S[x] to out[x], then the next block forwards,
+// replacing out[x] by S[x] (+) (prefix of the next block up to x + k - 1).
+// The second reads of a block and of its suffixes come from this thread's
+// recent accesses (L1/L2).  Four loads in flight in each walk.
+// ---------------------------------------------------------------------------
+template <class M, class SIn, class SOut>
+__global__ void __launch_bounds__(128)
+k_inc_strided_big(const SIn *__restrict__ in, SOut *__restrict__ out, int64_t O, int n, int64_t I, int k, int Lc,
+                  int nchunks)
+{
+    using Lt = typename M::loc_t;
+    const int64_t total = O * nchunks * I;
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= total) return;
+    const int64_t i = gid % I;
+    const int64_t rest = gid / I;
+    const int ch = (int)(rest % nchunks);
+    const int64_t o = rest / nchunks;
+    const SIn *src = in + o * n * I + i;
+    SOut *dst = out + o * n * I + i;
+    const int r0 = ch * Lc;
+    const int rend = min(r0 + Lc, n);
+    auto ld = [&](int x) { return M::lget(src[(int64_t)x * I]); };
+    for (int sb = r0; sb < rend; sb += k) {
+        const int be = min(sb + k, n);
+        // suffixes of the block, backwards
+        Lt s = M::lid();
+        int x = be - 1;
+        for (; x - 3 >= sb; x -= 4) {
+            Lt v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) v[u] = ld(x - u);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                s = M::lop(v[u], s);
+                dst[(int64_t)(x - u) * I] = M::template lput<SOut>(s);
+            }
+        }
+        for (; x >= sb; --x) {
+            s = M::lop(ld(x), s);
+            dst[(int64_t)x * I] = M::template lput<SOut>(s);
+        }
+        // out[sb] is the block's total; later outputs add the next block's prefix
+        Lt p = M::lid();
+        int xo = sb + 1;
+        for (; xo + 3 < be; xo += 4) {
+            Lt v[4], sv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int y = xo + u + k - 1;
+                v[u] = y < n ? ld(y) : M::lid();
+                sv[u] = M::lget(dst[(int64_t)(xo + u) * I]);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                p = M::lop(p, v[u]);
+                dst[(int64_t)(xo + u) * I] = M::template lput<SOut>(M::lop(sv[u], p));
+            }
+        }
+        for (; xo < be; ++xo) {
+            const int y = xo + k - 1;
+            if (y < n) p = M::lop(p, ld(y));
+            dst[(int64_t)xo * I] = M::template lput<SOut>(M::lop(M::lget(dst[(int64_t)xo * I]), p));
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Rows [ya, yb) of column c of a view [*, Mc], reduced with short fp32 runs
 // (at most 32 rows) combined into the long accumulator.
 // ---------------------------------------------------------------------------

@@ -327,10 +327,12 @@ __device__ __forceinline__ typename M::acc_t warp_sum0(typename M::acc_t v)
     return shfl_idx(v, 0);
 }
 
+// kwin: planes of R combined into H1 -- k1, or 1 when R already holds the
+// window sums along x1 (H1 itself, from a strided BDBS pass).
 template <class M, class SR = typename M::car_t, class ST = typename M::car_t>
 __device__ __forceinline__ void k_exc2d_w_body(const SR *__restrict__ R, const typename M::car_t *__restrict__ R2,
                                                ST *__restrict__ T, int n1, int n2, int k1, int k2, int64_t vbid,
-                                               int64_t vgrid)
+                                               int64_t vgrid, int kwin)
 {
     using A = typename M::acc_t;
     extern __shared__ __align__(16) unsigned char e2w_smem[];
@@ -346,7 +348,7 @@ __device__ __forceinline__ void k_exc2d_w_body(const SR *__restrict__ R, const t
     for (int y = lane; y < n1; y += 32)
         if (y < x1 || y >= x1 + k1) t2 = M::op(t2, M::get(R2[y]));
     t2 = warp_sum0<M>(t2);
-    const int kw = min(k1, n1 - x1);
+    const int kw = min(kwin, n1 - x1);
     const SR *row = R + (int64_t)x1 * n2;
     const int nc = (n2 + 31) >> 5;
     A carry = M::id();
@@ -404,7 +406,7 @@ __global__ void __launch_bounds__(256)
 k_exc2d_w(const SR *__restrict__ R, const typename M::car_t *__restrict__ R2, ST *__restrict__ T, int n1, int n2,
           int k1, int k2)
 {
-    k_exc2d_w_body<M, SR, ST>(R, R2, T, n1, n2, k1, k2, blockIdx.x, gridDim.x);
+    k_exc2d_w_body<M, SR, ST>(R, R2, T, n1, n2, k1, k2, blockIdx.x, gridDim.x, k1);
 }
 
 // Warps per block of k_exc2d_w for rows of n2 accumulators of `acc` bytes:

@@ -34,6 +34,11 @@ enum LvKind : int {
     LV_RX_K1_E4, LV_RX_K1_E8, LV_RX_K1_E16, LV_RX_K1_E32,
     LV_RX_K8_E4, LV_RX_K8_E8, LV_RX_K8_E16, LV_RX_K8_E32,
     LV_RX_K32_E4, LV_RX_K32_E8, LV_RX_K32_E16, LV_RX_K32_E32,
+    // window sums along x1 of the lower problem's input (H1), from the carry
+    // type (d = 3: R) or the input type (d = 2: X), window bound 4 .. 32
+    LV_H1C_K4, LV_H1C_K8, LV_H1C_K16, LV_H1C_K32,
+    LV_H1I_K4, LV_H1I_K8, LV_H1I_K16, LV_H1I_K32,
+    LV_E2_CO,                            // lower problem from H1 (carry type) into the output (d = 2)
     LV_KINDS
 };
 
@@ -104,6 +109,7 @@ __device__ __forceinline__ void lv_pull(const LvList &ls, F run)
 __host__ __device__ constexpr int lv_class(int kind)
 {
     if (kind == LV_S1_K32 || kind == LV_S4_K8) return 1;
+    if (kind == LV_H1C_K32 || kind == LV_H1I_K32) return 1;
     if (kind >= LV_RX_K1_E4 && kind <= LV_RX_K32_E32) {
         const int km = (kind - LV_RX_K1_E4) / 4, e = (kind - LV_RX_K1_E4) % 4;   // km 0: 1, 1: 8, 2: 32
         if (e == 3) return 2;
@@ -182,6 +188,46 @@ kl_plane(LvList ls)
     });
 }
 
+// ---- window sums along x1 of the lower problem (128 threads) ---------------------
+// M is the monoid of the carries; the strided BDBS pass over the view
+// [1, n1, n2] of R (or X), into H1 in the carry type.
+template <class M, int CLS, bool PERSIST>
+__global__ void __launch_bounds__(128, CLS == 0 ? 6 : 3)
+kl_lower_h1(LvList ls)
+{
+    using IN = typename M::in_t;
+    using C = typename M::car_t;
+    lv_pull<PERSIST>(ls, [&](const LvItem &w, int64_t vb) {
+        C *dst = static_cast<C *>(w.dst);
+        const C *sc = static_cast<const C *>(w.src);
+        const IN *si = static_cast<const IN *>(w.src);
+        auto hc = [&](auto kk) {
+            k_inc_strided_body<M, C, C, decltype(kk)::value>(sc, dst, w.O, w.n, w.I, w.k, w.Lc, w.nchunks, vb,
+                                                             w.vgrid);
+        };
+        auto hi = [&](auto kk) {
+            k_inc_strided_body<M, IN, C, decltype(kk)::value>(si, dst, w.O, w.n, w.I, w.k, w.Lc, w.nchunks, vb,
+                                                              w.vgrid);
+        };
+        if constexpr (CLS == 0) {
+            switch (w.kind) {
+            case LV_H1C_K4: hc(std::integral_constant<int, 4>()); break;
+            case LV_H1C_K8: hc(std::integral_constant<int, 8>()); break;
+            case LV_H1C_K16: hc(std::integral_constant<int, 16>()); break;
+            case LV_H1I_K4: hi(std::integral_constant<int, 4>()); break;
+            case LV_H1I_K8: hi(std::integral_constant<int, 8>()); break;
+            default: hi(std::integral_constant<int, 16>()); break;
+            }
+        } else {
+            if (w.kind == LV_H1C_K32)
+                hc(std::integral_constant<int, 32>());
+            else
+                hi(std::integral_constant<int, 32>());
+        }
+        return true;
+    });
+}
+
 // ---- the two-dimensional lower problem (128 threads): one warp per x1 ----------
 // d = 3: T = excluded(R) in the carry type; d = 2: the output itself.
 template <class M, bool PERSIST>
@@ -193,36 +239,41 @@ kl_exc2d(LvList ls)
     using C = typename M::car_t;
     lv_pull<PERSIST>(ls, [&](const LvItem &w, int64_t vb) {
         const C *R2 = static_cast<const C *>(w.t);
+        const int kwin = w.Lc > 0 ? w.Lc : w.k;   // Lc: planes per window read here (1: H1 given)
         if (w.kind == LV_E2_IN)
             k_exc2d_w_body<M, IN, OUT>(static_cast<const IN *>(w.src), R2, static_cast<OUT *>(w.dst), w.n, w.n2,
-                                       w.k, w.k2, vb, w.vgrid);
+                                       w.k, w.k2, vb, w.vgrid, kwin);
+        else if (w.kind == LV_E2_CO)
+            k_exc2d_w_body<M, C, OUT>(static_cast<const C *>(w.src), R2, static_cast<OUT *>(w.dst), w.n, w.n2,
+                                      w.k, w.k2, vb, w.vgrid, kwin);
         else
             k_exc2d_w_body<M, C, C>(static_cast<const C *>(w.src), R2, static_cast<C *>(w.dst), w.n, w.n2, w.k,
-                                    w.k2, vb, w.vgrid);
+                                    w.k2, vb, w.vgrid, kwin);
         return true;
     });
 }
 
 // ---- final pass, staged by bulk copies (256 threads, two blocks per SM) ----------
-template <class M, int KMAX>
+template <class M, int KMAX, bool ODD>
 __device__ __forceinline__ bool lv_bulk(const LvItem &w, int64_t vb)
 {
     using Lt = typename M::loc_t;
     using OUT = typename M::out_t;
-    return k_rowx_bulk_body<M, OUT, KMAX, 32, 2, 256, 0>(
+    return k_rowx_bulk_body<M, OUT, KMAX, 32, 2, 256, 0, ODD>(
         static_cast<const Lt *>(w.src), static_cast<const typename M::car_t *>(w.t), static_cast<OUT *>(w.dst),
         w.ntiles, w.ntile, w.n2, w.L, w.k2, w.k3, w.TR, w.LSW, w.lpr, w.aligned, vb, w.vgrid);
 }
 
-template <class M, bool PERSIST>
+// ODD: rows whose length is not a multiple of 4 (a launch of their own)
+template <class M, bool PERSIST, bool ODD>
 __global__ void __launch_bounds__(256, 2)
 kl_final_bulk(LvList ls)
 {
     lv_pull<PERSIST>(ls, [&](const LvItem &w, int64_t vb) -> bool {
         switch (w.kind) {
-        case LV_BK_K1: return lv_bulk<M, 1>(w, vb);
-        case LV_BK_K8: return lv_bulk<M, 8>(w, vb);
-        default: return lv_bulk<M, 32>(w, vb);
+        case LV_BK_K1: return lv_bulk<M, 1, ODD>(w, vb);
+        case LV_BK_K8: return lv_bulk<M, 8, ODD>(w, vb);
+        default: return lv_bulk<M, 32, ODD>(w, vb);
         }
     });
 }

@@ -207,4 +207,114 @@ k_carry_blk(const typename M::car_t *__restrict__ R, const typename M::car_t *__
     }
 }
 
+// ---------------------------------------------------------------------------
+// BDBS along the contiguous dimension for long boxes (k > 32): one warp per
+// segment of G elements of a row (G a multiple of k, so segments hold whole
+// blocks), in chunks of 32 consecutive elements, one per lane.
+//   Backwards over the segment: the suffix of every element within its block
+//   of k (a segmented warp scan: lanes whose elements lie in the same block
+//   combine; the block continuing from the chunk before is carried in), into
+//   out.
+//   Forwards over the elements y the segment's windows reach in the next
+//   blocks: the prefix of y within its block, the same way, and
+//   out[y - k + 1] = S (+) prefix -- except where y - k + 1 starts a block
+//   (its window is the whole block: the suffix alone).
+//   Windows cut by the row's end take the prefix of the last element.
+// Input read twice and out read once besides its two writes, all coalesced.
+// ---------------------------------------------------------------------------
+template <class M, class SIn, class SOut>
+__global__ void __launch_bounds__(256)
+k_inc_rows_big(const SIn *__restrict__ in, SOut *__restrict__ out, int64_t rows, int64_t L, int64_t k, int64_t G,
+               int64_t nseg)
+{
+    using Lt = typename M::loc_t;
+    const int lane = threadIdx.x & 31;
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (w >= rows * nseg) return;   // whole warps
+    const int64_t row = w / nseg, sg = w - row * nseg;
+    const SIn *src = in + row * L;
+    SOut *dst = out + row * L;
+    const int64_t a = sg * G, e = min(a + G, L);
+    // segmented inclusive scan across the lanes in lane order; blk: block of the lane's element
+    auto seg_scan = [&](Lt v, int64_t blk) -> Lt {
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const Lt u = shfl_up(v, d);
+            const int64_t bu = shfl_up(blk, d);
+            if (lane >= d && bu == blk) v = M::lop(u, v);
+        }
+        return v;
+    };
+    // backwards: suffixes within blocks, four chunks per round (their loads
+    // in flight together)
+    Lt carry = M::lid();
+    int64_t carry_blk = -1;
+    // (block indices: one division per chunk; k > 32, so a chunk meets at
+    // most two blocks)
+    for (int64_t r0 = 0; r0 < e - a; r0 += 128) {
+        Lt v[4];
+        int64_t xs[4], blks[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t xh = e - 1 - r0 - 32 * u;   // the chunk's first (highest) element
+            const int64_t bh = xh / k, oh = xh - bh * k;
+            const int64_t x = xh - lane;
+            const bool ok = x >= a;
+            xs[u] = x;
+            blks[u] = ok ? (lane <= oh ? bh : bh - 1) : -2 - lane;
+            v[u] = ok ? M::lget(src[x]) : M::lid();
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            Lt t = seg_scan(v[u], blks[u]);
+            if (blks[u] == carry_blk) t = M::lop(t, carry);
+            if (xs[u] >= a) dst[xs[u]] = M::template lput<SOut>(t);
+            carry = shfl_idx(t, 31);
+            carry_blk = shfl_idx(blks[u], 31);
+        }
+    }
+    __syncwarp();
+    // forwards: prefixes of the next blocks, combined
+    const int64_t y0 = a + k, y1 = min(a + G + k - 1, L);
+    carry = M::lid();
+    carry_blk = -1;
+    Lt last = M::lid();   // prefix of the row's last element, once reached
+    for (int64_t r0 = y0; r0 < y1; r0 += 128) {
+        Lt v[4], sv[4];
+        int64_t blks[4], yms[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t t0 = r0 + 32 * u;
+            const int64_t b0 = t0 / k, o0 = t0 - b0 * k;
+            const int64_t y = t0 + lane;
+            const bool ok = y < y1;
+            const bool wrap = o0 + lane >= k;
+            blks[u] = ok ? (wrap ? b0 + 1 : b0) : -2 - lane;
+            yms[u] = wrap ? o0 + lane - k : o0 + lane;   // y mod k
+            v[u] = ok ? M::lget(src[y]) : M::lid();
+            sv[u] = (ok && yms[u] != k - 1) ? M::lget(dst[y - k + 1]) : M::lid();
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t y = r0 + 32 * u + lane;
+            Lt t = seg_scan(v[u], blks[u]);
+            if (blks[u] == carry_blk) t = M::lop(t, carry);
+            if (y < y1 && yms[u] != k - 1) dst[y - k + 1] = M::template lput<SOut>(M::lop(sv[u], t));
+            if (y == L - 1) last = t;
+            carry = shfl_idx(t, 31);
+            carry_blk = shfl_idx(blks[u], 31);
+        }
+    }
+    // the lane that held y = L - 1 shares its prefix
+    unsigned has = __ballot_sync(0xffffffffu, y1 == L && (L - 1 - y0) >= 0 && ((L - 1 - y0) & 31) == lane &&
+                                                  L - 1 >= y0);
+    if (has) last = shfl_idx(last, __ffs(has) - 1);
+    __syncwarp();
+    // windows cut by the row's end
+    for (int64_t x = max(a, L - k + 1) + lane; x < e; x += 32) {
+        if (x % k == 0) continue;   // a block start: the suffix alone
+        if ((x / k + 1) * k < L && has) dst[x] = M::template lput<SOut>(M::lop(M::lget(dst[x]), last));
+    }
+}
+
 }  // namespace exsum

@@ -133,20 +133,35 @@ __host__ __device__ inline int rowbulk_stage_rows(int TR, int k2, bool aligned)
 }
 
 // Column width of the window walk and the number of row segments per
-// column group for a block of nt threads.
-__host__ __device__ constexpr int rowbulk_cw(int kmax) { return kmax <= 8 ? 4 : (kmax <= 16 ? 2 : 1); }
-__host__ __device__ inline int rowbulk_segs(int L, int kmax, int nt)
+// column group for a block of nt threads.  Rows whose length is not a
+// multiple of 4 (odd) sit at every alignment in the staging buffer: the walk
+// reads them one element at a time.
+__host__ __device__ constexpr int rowbulk_cw(int kmax, bool odd = false)
 {
-    const int lq = L / rowbulk_cw(kmax);
+    return odd ? 1 : (kmax <= 8 ? 4 : (kmax <= 16 ? 2 : 1));
+}
+__host__ __device__ inline int rowbulk_segs(int L, int kmax, int nt, bool odd = false)
+{
+    const int lq = L / rowbulk_cw(kmax, odd);
     return lq >= nt ? 1 : nt / lq;
+}
+
+// Elements of one staging buffer: the rows, and for odd rows room for the
+// shift (0 .. 3 elements) that puts the copy's source on a 16-byte
+// boundary, rounded to whole 16-byte chunks.
+__host__ __device__ inline int rowbulk_stage_elems(int rows, int L, bool odd)
+{
+    return odd ? (rows * L + 3 + 3) & ~3 : rows * L;
 }
 
 // Shared memory of one block (bytes): NBUF barriers (128 bytes), NBUF
 // staging buffers, the row buffer W (TR rows of LSW elements) and a 16-byte
 // identity chunk.
-__host__ __device__ inline size_t rowbulk_smem(int TR, int k2, bool aligned, int L, int LSW, int nbuf)
+__host__ __device__ inline size_t rowbulk_smem(int TR, int k2, bool aligned, int L, int LSW, int nbuf,
+                                               bool odd = false)
 {
-    return 128 + (size_t)nbuf * rowbulk_stage_rows(TR, k2, aligned) * L * 4 + (size_t)TR * LSW * 4 + 16;
+    return 128 + (size_t)nbuf * rowbulk_stage_elems(rowbulk_stage_rows(TR, k2, aligned), L, odd) * 4 +
+           (size_t)TR * LSW * 4 + 16;
 }
 
 // Window walk of one column group of CW adjacent elements over output rows
@@ -274,8 +289,9 @@ __device__ __forceinline__ void rowbulk_walk(const typename M::loc_t *__restrict
 
 // ---------------------------------------------------------------------------
 // The kernel.  Requirements (checked by the planner): the input has the
-// local type (4 bytes), L % 4 == 0, 128 <= L <= 1024, `in` and `out` 16-byte
-// aligned, lpr = LP / EPL a power of two in [4, 32] with LP >= L, LSW =
+// local type (4 bytes), 128 <= L <= 1024, L % 4 == 0 unless ODD (rows of
+// any length: copies and stores realigned, see `issue` and the copy-out),
+// `in` and `out` 16-byte aligned, lpr = LP / EPL a power of two in [4, 32] with LP >= L, LSW =
 // LP rounded up to 32, k2 <= KMAX, TR a multiple of (NT / 32) * (32 / lpr)
 // (the rows one pass of the row phase covers), ntiles < 2^31, smem =
 // rowbulk_smem(...).  `aligned` (k2 == KMAX and TR a multiple of the
@@ -288,7 +304,7 @@ __device__ __forceinline__ void rowbulk_walk(const typename M::loc_t *__restrict
 // A block that gives up waiting counts itself in g_wait_timeouts and
 // returns (never expected).
 // ---------------------------------------------------------------------------
-template <class M, class SOut, int KMAX, int EPL, int NBUF, int NT, int LT>
+template <class M, class SOut, int KMAX, int EPL, int NBUF, int NT, int LT, bool ODD = false>
 __device__ __forceinline__ bool
 k_rowx_bulk_body(const typename M::loc_t *__restrict__ in, const typename M::car_t *__restrict__ T,
                  SOut *__restrict__ out, int ntiles, int ntile, int n2, int L_, int k2, int k3, int TR,
@@ -300,14 +316,16 @@ k_rowx_bulk_body(const typename M::loc_t *__restrict__ in, const typename M::car
     using Lt = typename M::loc_t;
     using A = typename M::acc_t;
     static_assert(sizeof(Lt) == 4 && sizeof(SOut) == 4, "4-byte local and output types");
-    constexpr int CW = rowbulk_cw(KMAX);
+    static_assert(!ODD || LT == 0, "odd rows have a run-time length");
+    constexpr int CW = rowbulk_cw(KMAX, ODD);
     constexpr int NW = NT / 32;
     extern __shared__ __align__(128) unsigned char rb_smem[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(rb_smem);
     const bool al = LT > 0 || aligned != 0;
     const int RSA = rowbulk_stage_rows(TR, k2, al);
+    const int SB = rowbulk_stage_elems(RSA, L, ODD);   // elements per staging buffer
     Lt *stage0 = reinterpret_cast<Lt *>(rb_smem + 128);
-    Lt *W = stage0 + NBUF * RSA * L;
+    Lt *W = stage0 + NBUF * SB;
     Lt *idc = W + TR * LSW;   // 4 identity elements
     const int LP = lpr * EPL;
     const int rpw = 32 / lpr;
@@ -331,9 +349,11 @@ k_rowx_bulk_body(const typename M::loc_t *__restrict__ in, const typename M::car
             }
         }
     }
-    // staging rows past the halo (read by the walk, never copied into)
-    for (int b = 0; b < NBUF; ++b)
-        for (int i = tid; i < (RSA - (TR + halo)) * L; i += NT) stage0[(b * RSA + TR + halo) * L + i] = M::lid();
+    // staging rows past the halo (read by the walk, never copied into; odd
+    // rows: filled with each tile, at its shift)
+    if constexpr (!ODD)
+        for (int b = 0; b < NBUF; ++b)
+            for (int i = tid; i < (RSA - (TR + halo)) * L; i += NT) stage0[b * SB + (TR + halo) * L + i] = M::lid();
 
     // Column groups and row segments of the walk, fixed for the kernel.
     // (aligned walk: the planner's segments of whole k2-blocks; generic
@@ -360,15 +380,34 @@ k_rowx_bulk_body(const typename M::loc_t *__restrict__ in, const typename M::car
     // Stages tile t into buffer b: identity in rows [nst, TR + halo) first
     // (all threads; ordered before the walk by the barriers in between),
     // then one bulk copy by thread 0.
+    // Odd rows: the tile's first element lies at element offset sh (0 .. 3)
+    // of the buffer, so that the copy starts on a 16-byte boundary of the
+    // input; the copy ends on the last such boundary inside the tile, and
+    // the at most 3 elements after it are loaded by plain loads.
     auto issue = [&](int o, int a, int b) {
         const int nst = min(TR + halo, n2 - a);
-        Lt *st = stage0 + b * RSA * L;
-        for (int i = tid; i < (TR + halo - nst) * L; i += NT) st[nst * L + i] = M::lid();
-        if (tid == 0) {
-            fence_proxy_async_smem();
-            const unsigned bytes = (unsigned)nst * (unsigned)L * 4u;
-            mbar_arrive_expect_tx(bar + b, bytes);
-            bulk_g2s(st, in + ((int64_t)o * n2 + a) * (int64_t)L, bytes, bar + b, pol_in);
+        Lt *st = stage0 + b * SB;
+        const int64_t e0g = ((int64_t)o * n2 + a) * (int64_t)L;
+        if constexpr (ODD) {
+            const int sh = (int)(e0g & 3);
+            const int64_t e1g = e0g + (int64_t)nst * L;
+            const int64_t g0 = e0g - sh, gend = e1g & ~(int64_t)3;
+            for (int i = tid; i < (RSA - nst) * L; i += NT) st[sh + nst * L + i] = M::lid();
+            if (tid < (int)(e1g - gend)) st[(int)(gend - g0) + tid] = in[gend + tid];
+            if (tid == 0) {
+                fence_proxy_async_smem();
+                const unsigned bytes = gend > g0 ? (unsigned)(gend - g0) * 4u : 0u;
+                mbar_arrive_expect_tx(bar + b, bytes);
+                if (bytes) bulk_g2s(st, in + g0, bytes, bar + b, pol_in);
+            }
+        } else {
+            for (int i = tid; i < (TR + halo - nst) * L; i += NT) st[nst * L + i] = M::lid();
+            if (tid == 0) {
+                fence_proxy_async_smem();
+                const unsigned bytes = (unsigned)nst * (unsigned)L * 4u;
+                mbar_arrive_expect_tx(bar + b, bytes);
+                bulk_g2s(st, in + e0g, bytes, bar + b, pol_in);
+            }
         }
     };
 
@@ -428,7 +467,8 @@ k_rowx_bulk_body(const typename M::loc_t *__restrict__ in, const typename M::car
         const int o = o_cur;
         const int a = j_cur * TR;
         const int nout = min(TR, n2 - a);
-        const Lt *stage = stage0 + b * RSA * L;
+        const Lt *stage = stage0 + b * SB;
+        if constexpr (ODD) stage += (int)((((int64_t)o * n2 + a) * (int64_t)L) & 3);
         int ok = 1;
         if (tid == 0) ok = mbar_wait_bounded(bar + b, parity) ? 1 : 0;
         if (!__syncthreads_and(ok)) {
@@ -535,9 +575,50 @@ k_rowx_bulk_body(const typename M::loc_t *__restrict__ in, const typename M::car
                 for (int m = 0; m < 4; ++m) o4[m] = finish<M, SOut>(tv, res[4 * i + m]);
                 uint4 w;
                 memcpy(&w, o4, 16);
-                if (LP == L || e0 + 4 * i < L) *reinterpret_cast<uint4 *>(row + toff[i]) = w;
+                if (LP == L || e0 + 4 * i + 4 <= L) {
+                    *reinterpret_cast<uint4 *>(row + toff[i]) = w;
+                } else if (ODD && e0 + 4 * i < L) {
+                    // the chunk holding the row's end: its columns past L stay identity
+#pragma unroll
+                    for (int m = 0; m < 4; ++m)
+                        if (e0 + 4 * i + m < L) row[toff[i] + m] = o4[m];
+                }
             }
             __syncwarp();
+            if constexpr (ODD) {
+                // the warp's rows are one contiguous run of the output, which
+                // starts at any alignment: its whole 16-byte chunks with
+                // 16-byte stores, the at most 3 elements before and after
+                // them with plain ones
+                const int q = min(rpw, nout - rb);
+                const int64_t F0 = (rowbase + rb) * (int64_t)L, F1 = F0 + (int64_t)q * L;
+                const int64_t G0 = min(F1, (F0 + 3) & ~(int64_t)3), G1 = max(G0, F1 & ~(int64_t)3);
+                // (W holds the results' bits)
+                auto wv = [&](int rel) {
+                    const int rr = rel / L;
+                    SOut v;
+                    memcpy(&v, W + (rb + rr) * LSW + tswz<Lt>(rel - rr * L), 4);
+                    return v;
+                };
+                if (lane < (int)(G0 - F0)) st_hint(out + F0 + lane, wv(lane), pol_out);
+                if (lane < (int)(F1 - G1)) st_hint(out + G1 + lane, wv((int)(G1 - F0) + lane), pol_out);
+                for (int64_t f = G0 + 4 * lane; f < G1; f += 128) {
+                    const int rel = (int)(f - F0);
+                    int rr = rel / L, cc = rel - rr * L;
+                    Lt o4[4];
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) {
+                        o4[m] = W[(rb + rr) * LSW + tswz<Lt>(cc)];
+                        if (++cc == L) {
+                            cc = 0;
+                            ++rr;
+                        }
+                    }
+                    uint4 w;
+                    memcpy(&w, o4, 16);
+                    st_hint_v4(out + f, w, pol_out);
+                }
+            } else
             // coalesced copy-out of this warp's rows
             for (int q = 0; q < rpw; ++q) {
                 const int rr = rb + q;
@@ -562,14 +643,14 @@ k_rowx_bulk_body(const typename M::loc_t *__restrict__ in, const typename M::car
     return true;
 }
 
-template <class M, class SOut, int KMAX, int EPL, int NBUF, int NT, int LT>
+template <class M, class SOut, int KMAX, int EPL, int NBUF, int NT, int LT, bool ODD = false>
 __global__ void __launch_bounds__(NT, 512 / NT)
 k_rowx_bulk(const typename M::loc_t *__restrict__ in, const typename M::car_t *__restrict__ T,
             SOut *__restrict__ out, int ntiles, int ntile, int n2, int L_, int k2, int k3, int TR,
             int LSW_, int lpr_, int aligned)
 {
-    k_rowx_bulk_body<M, SOut, KMAX, EPL, NBUF, NT, LT>(in, T, out, ntiles, ntile, n2, L_, k2, k3, TR, LSW_, lpr_,
-                                                     aligned, blockIdx.x, gridDim.x);
+    k_rowx_bulk_body<M, SOut, KMAX, EPL, NBUF, NT, LT, ODD>(in, T, out, ntiles, ntile, n2, L_, k2, k3, TR, LSW_,
+                                                          lpr_, aligned, blockIdx.x, gridDim.x);
 }
 
 }  // namespace exsum

@@ -34,7 +34,7 @@ bool level_accepts(const exsum_desc &d, int sms);
 // branches are created here, outside any capture.
 int level_create(const exsum_desc *descs, const int *idx, int n, const LevelTune &tune, LevelSet **out);
 
-// Enqueues the level set on `s` (capturable): at most ten kernels (and,
+// Enqueues the level set on `s` (capturable): at most thirteen kernels (and,
 // for persistent grids, one memset of the work-list counters), in up to
 // three parallel branches.
 int level_enqueue(LevelSet *ls, cudaStream_t s);

@@ -229,7 +229,32 @@ struct Pipe {
                 inc_fast<SIn, SOut, 32>(cx, src, dst, O, n, I, k);
             return;
         }
-        // Large boxes: per-thread suffix slots in shared or global memory.
+        // Large boxes along a strided dimension: one block of k lines per
+        // thread, the block's suffixes kept in the output (k_inc_strided_big).
+        if (I > 1 && n < (1ll << 30) && env_int("EXSUM_BIGK", 1) != 0) {
+            if (cx.dry) return;
+            const int64_t nchunks = cdiv(n, k);
+            const int64_t total = O * nchunks * I;
+            cx.before(TAG_INC_STRIDED, O * n * I);
+            k_inc_strided_big<M, SIn, SOut><<<(unsigned)cdiv(total, 128), 128, 0, cx.stream>>>(
+                src, dst, O, (int)n, I, (int)k, (int)k, (int)nchunks);
+            cx.check_launch();
+            return;
+        }
+        // Large boxes along the contiguous dimension: one warp per segment of
+        // whole blocks of a row (k_inc_rows_big).
+        if (I == 1 && env_int("EXSUM_BIGK", 1) != 0) {
+            if (cx.dry) return;
+            const int64_t G = k * (k < 1024 ? 1024 / k : 1);
+            const int64_t nseg = cdiv(n, G);
+            const int64_t warps = O * nseg;
+            cx.before(TAG_INC_CONTIG, O * n);
+            k_inc_rows_big<M, SIn, SOut><<<(unsigned)cdiv(warps * 32, 256), 256, 0, cx.stream>>>(
+                src, dst, O, n, k, G, nseg);
+            cx.check_launch();
+            return;
+        }
+        // Otherwise: per-thread suffix slots in shared or global memory.
         int threads = INC_THREADS;
         while (threads > 32 && (size_t)k * threads * sizeof(A) > SLOT_SMEM_MAX) threads >>= 1;
         const bool global_slots = (size_t)k * threads * sizeof(A) > SLOT_SMEM_MAX;
@@ -491,7 +516,7 @@ struct Pipe {
 
     // ---- final pass staged by bulk copies (kernels_rowbulk.cuh) ---------------------------
     struct BulkPlan {
-        bool ok = false, aligned = false, pdl = false;
+        bool ok = false, aligned = false, pdl = false, odd = false;
         int TR = 0, epl = 32, lpr = 8, LSW = 0, nbuf = 2, nt = 256;
         size_t smem = 0;
         int ntiles = 0, grid = 0, ntile = 0;
@@ -517,7 +542,9 @@ struct Pipe {
         BulkPlan bp;
         // (shorter rows stay with k_rowx: tiles of a few KB and walks over a
         // handful of columns cost more than the bulk copies save)
-        if (sizeof(L_) != 4 || (L & 3) || L < 128 || L > 1024 || kk > 32) return bp;
+        if (sizeof(L_) != 4 || L < 128 || L > 1024 || kk > 32) return bp;
+        const bool odd = (L & 3) != 0 && env_int("EXSUM_ROWX_ODD", 1) != 0;
+        if ((L & 3) && !odd) return bp;
         // strips of 32 elements, 4 .. 32 lanes per row
         const int epl = 32;
         int lpr = 4;
@@ -527,7 +554,7 @@ struct Pipe {
         const int nt = 256;
         const int nb_env = nbuf_force ? nbuf_force : env_int("EXSUM_ROWX_NBUF", 0);
         const int rows_pass = (nt / 32) * (32 / lpr);
-        const int G = rowbulk_segs((int)L, kmax, nt);
+        const int G = rowbulk_segs((int)L, kmax, nt, odd);
         // block-aligned walk when the tile can be a multiple of the segments
         // times the window (at most 64 rows), else the generic walk
         bool kfull = kk > 1 && kk == kmax;
@@ -542,7 +569,7 @@ struct Pipe {
         const int tr_env = tr_force ? tr_force : env_int("EXSUM_ROWX_TR", 0);
         auto sm = [&](int tr, int nb) {
             const bool al = kfull && (tr / G) % kk == 0 && tr % G == 0;
-            return rowbulk_smem(tr, kk, al, (int)L, LSW, nb);
+            return rowbulk_smem(tr, kk, al, (int)L, LSW, nb, odd);
         };
         const size_t two = 113 * 1024, one = 226 * 1024;
         // candidates in order of preference: (staging buffers, blocks per SM)
@@ -552,6 +579,7 @@ struct Pipe {
         for (int c = 0; c < 3 && !TR; ++c) {
             const int nb = cand[c][0];
             if (nb_env && nb != nb_env) continue;
+            if (odd && nb != 2) continue;
             const size_t lim = cand[c][1] == 2 ? two : one;
             if (tr_env > 0) {
                 const int tr = (tr_env + step - 1) / step * step;
@@ -572,6 +600,7 @@ struct Pipe {
         if (O2 * ntile >= (1ll << 31)) return bp;
         bp.ok = true;
         bp.aligned = kfull && (TR / G) % kk == 0 && TR % G == 0;
+        bp.odd = odd;
         bp.TR = TR;
         bp.epl = epl;
         bp.lpr = lpr;
@@ -585,11 +614,11 @@ struct Pipe {
         return bp;
     }
 
-    template <class SOut, int KM, int EPL, int NB, int NT, int LT = 0>
+    template <class SOut, int KM, int EPL, int NB, int NT, int LT = 0, bool ODD = false>
     static void rowbulk_go(Ctx &cx, const BulkPlan &bp, const L_ *src, const CAR *T, SOut *out,
                            int64_t n2, int64_t L, int kk, int k3)
     {
-        auto kern = k_rowx_bulk<M, SOut, KM, EPL, NB, NT, LT>;
+        auto kern = k_rowx_bulk<M, SOut, KM, EPL, NB, NT, LT, ODD>;
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bp.smem);
         if (bp.pdl)
             launch_pdl(kern, (unsigned)bp.grid, NT, bp.smem, cx.stream, src, T, out, bp.ntiles, bp.ntile,
@@ -604,6 +633,11 @@ struct Pipe {
     static void rowbulk_epl(Ctx &cx, const BulkPlan &bp, const L_ *src, const CAR *T, SOut *out,
                             int64_t n2, int64_t L, int kk, int k3)
     {
+        // rows of a length not a multiple of 4: two staging buffers only
+        if (bp.odd) {
+            rowbulk_go<SOut, KM, 32, 2, 256, 0, true>(cx, bp, src, T, out, n2, L, kk, k3);
+            return;
+        }
         // row lengths fixed at compile time for the common block-aligned cases
         if constexpr (KM == 4 || KM == 8) {
             if (bp.aligned && bp.LSW == L && bp.lpr * bp.epl == L) {
@@ -634,8 +668,8 @@ struct Pipe {
     }
 
     // Launches k_rowx_bulk when the pass qualifies (4-byte local type read
-    // as is, 16-byte aligned input and output, 128 <= L <= 1024, L % 4 == 0,
-    // no one-dimensional tail); returns false otherwise.
+    // as is, 16-byte aligned input and output, 128 <= L <= 1024, no
+    // one-dimensional tail); returns false otherwise.
     template <class SF, class SOut>
     static bool rowbulk_try(Ctx &cx, const SF *src, const CAR *T, SOut *out, int64_t O2, int64_t n2,
                             int64_t L, int kk, int k3, bool pdl = false)

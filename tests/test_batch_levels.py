@@ -37,6 +37,12 @@ EDGE = [
     ((64, 1024), (1, 1)),
     ((1, 16), (1, 16)),
     ((128, 77), (20, 31)),
+    # rows whose length is not a multiple of 4, bulk-staged
+    ((3, 70, 129), (2, 1, 5)),
+    ((2, 100, 131), (2, 4, 8)),
+    ((4, 33, 130), (3, 8, 130)),
+    ((2, 90, 255), (2, 16, 3)),
+    ((2, 40, 997), (2, 32, 500)),
 ]
 
 
@@ -85,7 +91,7 @@ def test_levels_64_small_uneven_tensors_match_oracle():
     rc, mode, nlevel = sched[:3]
     assert rc == 0 and mode == 1
     # every d = 2 tensor and every d = 3 tensor with rows of 16 .. 1024 joins
-    # at most nine level kernels and a memset, plus what the other tensors take alone
+    # at most thirteen level kernels and a memset, plus what the other tensors take alone
     lane = [(sh, k) for sh, k in spec if not (len(sh) == 2 or sh[-1] >= 16)]
     assert nlevel == len(spec) - len(lane)
     alone = 0
@@ -95,7 +101,7 @@ def test_levels_64_small_uneven_tensors_match_oracle():
         n0 = ex.exsum_launch_count()
         ex.excluded(x, k, "add")
         alone += ex.exsum_launch_count() - n0
-    assert info[4] <= 10 + alone
+    assert info[4] <= 14 + alone
 
 
 def test_levels_edge_shapes_and_a_mixed_lane():
@@ -111,7 +117,7 @@ def test_levels_batch_of_256_stays_within_a_few_kernels():
     spec = synth.batched_shapes(256, seed=9, side_lo=16, side_hi=64, k_lo=1, k_hi=32, cap=1 << 16)
     sched, info = _run(spec, ex.BATCH_LEVELS, 3000, replays=1)
     assert sched[1] == 1 and sched[2] == len(spec)
-    assert info[4] <= 9
+    assert info[4] <= 13
 
 
 def test_autotune_caches_its_choice(tmp_path, monkeypatch):

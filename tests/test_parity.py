@@ -168,3 +168,62 @@ def test_parity_many_planes(shape, k, dtype, op):
     got = gpu_sum("excluded", to_device(dev, dtype), k, op)
     check(got, oracle_sum("excluded", vals, k, op), dtype, op,
           "many planes %s %s %s k=%s" % (dtype, op, shape, k))
+
+
+# Boxes longer than 32 along a dimension: the strided passes keep each
+# block's suffixes in the output (one thread per block of k lines), the
+# contiguous passes run one warp per segment of whole blocks of a row.
+# Rows longer than a segment, boxes that do not divide the side, a box of the
+# whole side, boxes over 32 along every dimension, and d = 1.
+BIG_K = [
+    ((300, 40), (33, 37)),
+    ((5, 3000), (2, 255)),
+    ((70, 9, 130), (64, 9, 100)),
+    ((257, 33), (256, 33)),
+    ((3, 4, 2500), (3, 1, 1000)),
+    ((40, 50, 60), (40, 50, 60)),
+    ((12000,), (4000,)),
+    ((64, 1100), (1, 300)),
+]
+
+
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("dtype,op", [("f32", "add"), ("i64", "add"), ("i32", "max"), ("bf16", "add"),
+                                      ("f32", "max")])
+@pytest.mark.parametrize("shape,k", BIG_K, ids=[str(c[0]) + "k" + str(c[1]) for c in BIG_K])
+def test_parity_boxes_over_32(shape, k, dtype, op, kind):
+    seed = zlib.crc32(repr((shape, k, dtype, op, kind, "bigk")).encode()) & 0xFFFFFF
+    dev, vals = seeded(shape, dtype, seed, op)
+    got = gpu_sum(kind, to_device(dev, dtype), k, op)
+    check(got, oracle_sum(kind, vals, k, op), dtype, op,
+          "boxes over 32 %s %s %s %s k=%s" % (kind, dtype, op, shape, k))
+
+
+# Rows of 128 .. 1024 elements whose length is not a multiple of 4: the
+# bulk-staged final pass copies each tile from the 16-byte boundary before
+# it (the tile's data shifted by 0 .. 3 elements), loads the last elements
+# after the last boundary one by one, and writes every warp's rows as one
+# run realigned to 16-byte stores.  Windows along n_2 of each compile-time
+# bound (1, 4, 8, 16, 32), suffix offsets k_d both multiples of 4 and not,
+# several tiles per slice and a short last tile.
+ODD_ROWS = [
+    ((3, 70, 129), (2, 1, 5)),
+    ((2, 100, 131), (1, 4, 8)),
+    ((4, 33, 130), (3, 8, 130)),
+    ((2, 90, 255), (2, 16, 3)),
+    ((2, 40, 997), (1, 32, 500)),
+    ((1, 77, 1023), (1, 5, 1)),
+    ((5, 300, 150), (3, 7, 4)),
+    ((300, 131), (3, 9)),
+]
+
+
+@pytest.mark.parametrize("dtype,op", [("f32", "add"), ("i32", "max"), ("i32", "add"), ("f32", "max"),
+                                      ("bf16", "add")])
+@pytest.mark.parametrize("shape,k", ODD_ROWS, ids=[str(c[0]) + "k" + str(c[1]) for c in ODD_ROWS])
+def test_parity_odd_rows(shape, k, dtype, op):
+    seed = zlib.crc32(repr((shape, k, dtype, op, "odd")).encode()) & 0xFFFFFF
+    dev, vals = seeded(shape, dtype, seed, op)
+    got = gpu_sum("excluded", to_device(dev, dtype), k, op)
+    check(got, oracle_sum("excluded", vals, k, op), dtype, op,
+          "odd rows %s %s %s k=%s" % (dtype, op, shape, k))
