@@ -66,7 +66,9 @@ def parse_args(argv=None):
     p.add_argument("--requests", type=int, default=20000)
     p.add_argument("--profile-once", action="store_true",
                    help="run the workload's excluded sum twice without graphs or timing "
-                        "(a small, self-ending command for ncu) and exit")
+                        "(a small, self-ending command for ncu) and exit; with --mode batched, "
+                        "launch the 512-tensor batch's level schedule (tuning from "
+                        "EXSUM_LEVEL_TUNE) twice")
     return p.parse_args(argv)
 
 
@@ -729,6 +731,30 @@ def batched_bench(count, seed=11, steps=20, warmup=3, plain_steps=3):
         "plain": "the same tensors, one exsum_excluded_ws call each on one stream"}
 
 
+def run_batched_profile_once(count=512, seed=11):
+    """The batched workload's level schedule, planned without autotuning
+    (EXSUM_LEVEL_TUNE gives the tuning) and launched twice, for profilers."""
+    import torch
+
+    import paper_2106_00124_gb300 as ex
+    from paper_2106_00124_gb300 import synth
+    torch.cuda.set_device(0)
+    spec = synth.batched_shapes(count, seed=seed)
+    xs = _seeded_device_tensors([s_ for s_, _ in spec], seed, "f32")
+    outs = [torch.empty_like(x) for x in xs]
+    descs = [ex.make_desc(x.data_ptr(), o.data_ptr(), sh, k, ex.OP_ADD, ex.F32)
+             for x, o, (sh, k) in zip(xs, outs, spec)]
+    sp = torch.cuda.current_stream().cuda_stream
+    rc, plan = ex.exsum_batch_create(descs, lanes=ex.BATCH_LEVELS, stream=sp)
+    assert rc == 0, ex.strerror(rc)
+    for _ in range(2):
+        assert ex.exsum_batch_launch(plan, sp) == 0
+    torch.cuda.synchronize()
+    sched = ex.exsum_batch_schedule(plan)
+    ex.exsum_batch_destroy(plan)
+    print(json.dumps({"profile_once": "batched_%d" % count, "schedule": list(sched[1:])}))
+
+
 def run_batched(args):
     """The 512-tensor batched workload."""
     import torch
@@ -944,7 +970,10 @@ def run_served(args):
 def main(argv=None):
     args = parse_args(argv)
     if args.mode == "batched":
-        run_batched(args)
+        if args.profile_once:
+            run_batched_profile_once()
+        else:
+            run_batched(args)
         return
     if args.mode == "served":
         run_served(args)

@@ -84,7 +84,7 @@ void scan_dim_t(const SR *in, SW *out, SW *Cy, int d, const int64_t *n, int j, c
     if (p.nseg > 1) {
         const int64_t units = p.I == 1 ? p.O * p.nseg * 32 : p.O * p.nseg * p.I;
         k_scan_seg<M, SR, SW, SUF><<<(unsigned)cdiv(units, 256), 256, 0, s>>>(in, out, p.O, n[j], p.I, p.G, p.nseg);
-        k_seg_carry<M, SW, SUF><<<(unsigned)cdiv(p.O * p.I, 256), 256, 0, s>>>(out, Cy, p.O, n[j], p.I, p.G, p.nseg);
+        k_seg_carry<M, SW, SUF><<<(unsigned)cdiv(p.O * p.I * 32, 256), 256, 0, s>>>(out, Cy, p.O, n[j], p.I, p.G, p.nseg);
         k_seg_apply<M, SW, SUF><<<(unsigned)cdiv(p.O * n[j] * p.I, 256), 256, 0, s>>>(out, Cy, p.O, n[j], p.I,
                                                                                       p.G, p.nseg);
     } else if (p.I == 1) {

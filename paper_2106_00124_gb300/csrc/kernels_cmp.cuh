@@ -146,23 +146,38 @@ k_scan_seg(const SR *in, SW *out, int64_t O, int64_t n, int64_t I, int64_t G, in
 
 // Carries: Cy[(o * nseg + s) * I + i] = (+) of the totals of the segments
 // before s (SUF: after s) of line (o, i); a segment's total is its scan at
-// its last (SUF: first) element.
+// its last (SUF: first) element.  One warp per line: 32 segments at a time,
+// scanned across the lanes, each group carrying the total of the ones
+// before it.
 template <class M, class SW, bool SUF>
 __global__ void __launch_bounds__(256)
 k_seg_carry(const SW *__restrict__ out, SW *__restrict__ Cy, int64_t O, int64_t n, int64_t I, int64_t G,
             int64_t nseg)
 {
     using A = typename M::acc_t;
-    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (gid >= O * I) return;
-    const int64_t o = gid / I, i = gid - o * I;
+    const int lane = threadIdx.x & 31;
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (w >= O * I) return;   // whole warps
+    const int64_t o = w / I, i = w - o * I;
     A run = M::id();
-    for (int64_t t = 0; t < nseg; ++t) {
+    for (int64_t t0 = 0; t0 < nseg; t0 += 32) {
+        const int64_t t = t0 + lane;
         const int64_t sg = SUF ? nseg - 1 - t : t;
-        Cy[(o * nseg + sg) * I + i] = M::template put<SW>(run);
-        const int64_t a = sg * G, len = min(G, n - a);
-        const int64_t x = SUF ? a : a + len - 1;
-        run = M::op(run, M::get(out[(o * n + x) * I + i]));
+        A v = M::id();
+        if (t < nseg) {
+            const int64_t a = sg * G, len = min(G, n - a);
+            v = M::get(out[(o * n + (SUF ? a : a + len - 1)) * I + i]);
+        }
+        A inc = v;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const A u = shfl_up(inc, d);
+            if (lane >= d) inc = M::op(u, inc);
+        }
+        A ex = shfl_up(inc, 1);
+        if (lane == 0) ex = M::id();
+        if (t < nseg) Cy[(o * nseg + sg) * I + i] = M::template put<SW>(M::op(run, ex));
+        run = M::op(run, shfl_idx(inc, 31));
     }
 }
 

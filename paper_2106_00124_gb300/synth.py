@@ -91,6 +91,10 @@ WORKLOADS = {
     # 512^3 float32: larger than L2, for HBM-true per-pass figures
     "d3_512cube_f32_add_k8": dict(shape=(512, 512, 512), k=(8, 8, 8), dtype="f32", op="add",
                                   seed=10),
+    # rows whose length (301) is not a multiple of 4, larger than L2: the
+    # realigned bulk final pass
+    "d3_256x512x301_f32_add_k484": dict(shape=(256, 512, 301), k=(4, 8, 4), dtype="f32", op="add",
+                                        seed=11),
 }
 
 

@@ -19,7 +19,7 @@ pytestmark = pytest.mark.gpu
 
 FULL = ["d2_256x256_i64_add_k16", "d3_256cube_f32_add_k8", "d3_256cube_i32_max_k8",
         "d1_2p25_f32_add_k64", "d1_2p25_bf16_add_k64", "d4_76p4_f32_add_k4", "d4_76p4_bf16_add_k4",
-        "d5_32p5_f32_add_k4", "d5_32p5_bf16_add_k4"]
+        "d5_32p5_f32_add_k4", "d5_32p5_bf16_add_k4", "d3_256x512x301_f32_add_k484"]
 
 
 def _errors(got, ref):
