@@ -182,6 +182,13 @@ int exsum_excluded_noalloc(const void *in, void *out, int d, const int64_t *shap
  * device first).  Returns 0 or EXSUM_ECUDA. */
 int exsum_release_cached_workspace(void);
 
+/* Blocks of the bulk-staged final pass that gave up their bounded wait for a
+ * tile's copy (about a second) and returned without writing that tile's
+ * outputs, since the library was loaded, on the current device.  Never
+ * expected to be non-zero; a non-zero count means the affected results are
+ * wrong.  Reads device memory (synchronising with the device). */
+unsigned exsum_device_timeouts(void);
+
 /* ---------------------------------------------------------------------------
  * The paper's comparison methods on the GPU (baselines for box-complement;
  * same arguments, ownership and stream semantics as exsum_excluded).

@@ -112,6 +112,7 @@ _SIG = {
     "exsum_corners": ([_P, _P, ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                        ctypes.c_int, ctypes.c_int, _P], ctypes.c_int),
     "exsum_corner_region": ([ctypes.c_int, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+    "exsum_device_timeouts": ([], ctypes.c_uint),
     "exsum_slow_extra": ([ctypes.c_int], ctypes.c_int),
     "exsum_slow_run": ([_P, _P, ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                         ctypes.c_int, _P], ctypes.c_int),
@@ -309,6 +310,11 @@ def exsum_sat(in_ptr, out_ptr, d, shape, k, excluded, dtype, stream=0):
 
 def exsum_corners(in_ptr, out_ptr, d, shape, k, op, dtype, stream=0):
     return _load().exsum_corners(in_ptr, out_ptr, d, _arr(shape), _arr(k), op, dtype, stream or None)
+
+
+def exsum_device_timeouts():
+    """Blocks of the bulk final pass that gave up waiting for a copy (never expected)."""
+    return int(_load().exsum_device_timeouts())
 
 
 def exsum_corner_region(d, corner, dim):

@@ -523,6 +523,15 @@ int exsum_graph_exec_destroy(void *exec)
 }  // extern "C"
 
 namespace exsum {
+// Readers of the per-translation-unit counters of bulk-copy waits that gave
+// up (kernels_rowbulk.cuh), registered at load time.
+static std::vector<unsigned (*)()> &timeout_readers()
+{
+    static std::vector<unsigned (*)()> v;
+    return v;
+}
+void register_timeout_reader(unsigned (*reader)()) { timeout_readers().push_back(reader); }
+
 // For the other translation units (exsum_cmp.cu): argument checks and the
 // cached per-stream workspace.
 int validate_args(int d, const int64_t *shape, const int64_t *k, int op, int dtype)
@@ -545,6 +554,13 @@ int excluded_ws_serial(const void *in, void *out, int d, const int64_t *shape, c
 }  // namespace exsum
 
 extern "C" {
+
+unsigned exsum_device_timeouts(void)
+{
+    unsigned total = 0;
+    for (auto f : exsum::timeout_readers()) total += f();
+    return total;
+}
 
 int exsum_release_cached_workspace(void)
 {

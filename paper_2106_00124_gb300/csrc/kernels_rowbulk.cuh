@@ -42,6 +42,25 @@ namespace exsum {
 // translation unit; read by exsum_device_timeouts).  Never expected to move.
 static __device__ unsigned g_wait_timeouts;
 
+// Every translation unit registers a reader of its own counter with the
+// library (exsum_abi.cu), which adds them up.
+void register_timeout_reader(unsigned (*reader)());
+
+namespace {
+unsigned read_wait_timeouts()
+{
+    unsigned v = 0;
+    if (cudaMemcpyFromSymbol(&v, g_wait_timeouts, sizeof(v)) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return v;
+}
+struct WaitTimeoutsReader {
+    WaitTimeoutsReader() { register_timeout_reader(&read_wait_timeouts); }
+} g_wait_timeouts_reader;
+}  // namespace
+
 __device__ __forceinline__ uint32_t smem_addr(const void *p)
 {
     return (uint32_t)__cvta_generic_to_shared(p);

@@ -227,3 +227,19 @@ def test_parity_odd_rows(shape, k, dtype, op):
     got = gpu_sum("excluded", to_device(dev, dtype), k, op)
     check(got, oracle_sum("excluded", vals, k, op), dtype, op,
           "odd rows %s %s %s k=%s" % (dtype, op, shape, k))
+
+
+def test_no_bulk_copy_wait_gave_up():
+    """The bulk final pass's bounded waits for its tile copies never run out
+    (the library's counter of blocks that gave up stays at zero) over calls
+    through every bulk variant: even and odd row lengths, one and two
+    staging buffers."""
+    import torch
+
+    import paper_2106_00124_gb300 as ex
+    for shape, k in [((64, 256, 256), (8, 8, 8)), ((3, 70, 129), (2, 1, 5)), ((2, 40, 997), (1, 32, 500)),
+                     ((8, 300, 1024), (2, 16, 9))]:
+        x = torch.rand(shape, device="cuda") - 0.5
+        ex.excluded(x, k, "add")
+    torch.cuda.synchronize()
+    assert ex.exsum_device_timeouts() == 0
