@@ -17,6 +17,7 @@
 #include "kernels_flat.cuh"
 #include "kernels_fold.cuh"
 #include "kernels_line1d.cuh"
+#include "kernels_longrow.cuh"
 #include "kernels_rowbulk.cuh"
 #include "kernels_rows.cuh"
 
@@ -398,7 +399,7 @@ struct Pipe {
     static constexpr int64_t ROWX_TAIL = 4096;  // 1-D recursion folded into the final pass
 
     struct RowPlan {
-        bool ok = false, fuse = false;
+        bool ok = false, fuse = false, longrow = false;
         int GO = 1, TR = 1, ntile = 1, RS = 1, RSA = 1, LS = 16, lpr = 32, epl = 4;
         size_t smem = 0;
     };
@@ -698,6 +699,53 @@ struct Pipe {
         }
     }
 
+    // Rows longer than one warp scans (k_rowx_long, one block of 512 threads
+    // per row, strips of V = 4 .. 32 elements): the row schedule without the
+    // window along n_{d-1} in the final pass.  The local suffixes of a row
+    // stay in shared memory: up to 16384 elements of 4 bytes, 8192 of 8.
+    // Taken by default for d = 2 and rows of at most 4096 elements, where it
+    // measured faster than the dimension-1 schedule; EXSUM_LONGROW=2 takes it
+    // for every shape it can hold, 0 never.
+    static constexpr int LONGROW_NT = 512;
+    static RowPlan long_row_plan(int d, const int64_t *n)
+    {
+        RowPlan rp;
+        const int mode = env_int("EXSUM_LONGROW", 1);
+        if (d < 2 || mode == 0) return rp;
+        const int64_t L = n[d - 1];
+        const int64_t lmax = sizeof(L_) > 4 ? 512 : 1024;
+        const int64_t longmax = (int64_t)LONGROW_NT * (sizeof(L_) > 4 ? 16 : 32);
+        if (L <= lmax || L > longmax || n[d - 2] >= (1ll << 30)) return rp;
+        if (mode == 1 && (d != 2 || L > 4096)) return rp;
+        rp.ok = true;
+        rp.longrow = true;
+        rp.fuse = false;
+        return rp;
+    }
+
+    template <class SF, class SOut, int V>
+    static void rowx_long_v(Ctx &cx, const SF *src, const CAR *T, SOut *out, int64_t rows, int64_t L, int k3)
+    {
+        auto kern = k_rowx_long<M, SF, SOut, LONGROW_NT, V>;
+        const size_t smem = rowx_long_smem<M>(LONGROW_NT, V);
+        if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        const int64_t grid = rows < cx.sms * 3 ? rows : cx.sms * 3;
+        kern<<<(unsigned)grid, LONGROW_NT, smem, cx.stream>>>(src, T, out, rows, (int)L, k3);
+    }
+
+    template <class SF, class SOut>
+    static void rowx_long_go(Ctx &cx, const SF *src, const CAR *T, SOut *out, int64_t rows, int64_t L, int k3)
+    {
+        if (L <= LONGROW_NT * 4)
+            rowx_long_v<SF, SOut, 4>(cx, src, T, out, rows, L, k3);
+        else if (L <= LONGROW_NT * 8)
+            rowx_long_v<SF, SOut, 8>(cx, src, T, out, rows, L, k3);
+        else if (L <= LONGROW_NT * 16)
+            rowx_long_v<SF, SOut, 16>(cx, src, T, out, rows, L, k3);
+        else if constexpr (sizeof(L_) == 4)
+            rowx_long_v<SF, SOut, 32>(cx, src, T, out, rows, L, k3);
+    }
+
     template <class SF, class SOut>
     static void rowx_launch(Ctx &cx, const RowPlan &rp, const SF *src, const CAR *T, const CAR *R1, SOut *out,
                             int64_t O2, int64_t n2, int64_t L, int64_t k2, int64_t k3, bool pdl = false)
@@ -707,6 +755,11 @@ struct Pipe {
         const int k1 = R1 ? (int)k2 : 0;
         cx.before(TAG_ROWX, O2 * n2 * L);
         const int kk = rp.fuse ? (int)k2 : 1;
+        if (rp.longrow) {
+            rowx_long_go<SF, SOut>(cx, src, T, out, O2 * n2, L, (int)k3);
+            cx.check_launch();
+            return;
+        }
         if (!R1 && rowbulk_try<SF, SOut>(cx, src, T, out, O2, n2, L, kk, (int)k3, pdl)) {
             cx.check_launch();
             return;
@@ -829,7 +882,7 @@ struct Pipe {
         const bool lower2 = d == 3 && n[1] <= 4096 && k[0] <= 64 && n[0] <= SMALL2D_N1;
         bool fold = false;
         if constexpr (sizeof(L_) == 4 && sizeof(SOut) == 4)
-            fold = lower2 && P > 0 && dims[0] == 0 && (L % 128) == 0 && k[0] <= 8 &&
+            fold = lower2 && !rp.longrow && P > 0 && dims[0] == 0 && (L % 128) == 0 && k[0] <= 8 &&
                    env_int("EXSUM_FOLD", 1) != 0;
         CAR *R2 = lower2 ? cx.take<CAR>(n[0]) : nullptr;
         L_ *Rp = fold ? cx.take<L_>(rows * (L / 128)) : nullptr;
@@ -867,7 +920,7 @@ struct Pipe {
         // stream while the BDBS passes run on the caller's.  A one-dimensional
         // recursion of at most ROWX_TAIL elements is left to the final pass
         // (it needs only R).
-        const bool tail = d == 2 && n[0] <= ROWX_TAIL && k[0] <= 64;
+        const bool tail = !rp.longrow && d == 2 && n[0] <= ROWX_TAIL && k[0] <= 64;
         const Aux *aux = cx.aux;
         const bool fork = P > 0 && aux && aux->side && !cx.dry && cx.ok();
         cudaStream_t main_stream = cx.stream;
@@ -963,7 +1016,8 @@ struct Pipe {
             exc2d_launch<SIn, SOut>(cx, X, R2, out, n[0], n[1], k[0], k[1], true);
             return;
         }
-        const RowPlan rp = row_plan(d, n, k, cx.sms);
+        RowPlan rp = row_plan(d, n, k, cx.sms);
+        if (!rp.ok) rp = long_row_plan(d, n);
         if (rp.ok) {
             excluded_rows<SIn, SOut>(cx, rp, X, out, d, n, k);
             return;

@@ -243,3 +243,34 @@ def test_no_bulk_copy_wait_gave_up():
         ex.excluded(x, k, "add")
     torch.cuda.synchronize()
     assert ex.exsum_device_timeouts() == 0
+
+
+# Rows longer than one warp scans (1025 .. 16384 elements; 8-byte local
+# types up to 8192): the row schedule with one block per row in the final
+# pass (strips of 4 .. 32 elements per thread, compensated scans across
+# them).  Suffix offsets inside a strip, across strips and past the row end;
+# d = 2 (a one-dimensional lower problem) and d = 3.
+LONG_ROWS = [
+    ((5, 1025), (2, 1)),
+    ((7, 2048), (3, 700)),
+    ((3, 3001), (1, 33)),
+    ((4, 4097), (4, 4097)),
+    ((2, 3, 8192), (2, 2, 5)),
+    ((3, 2, 16384), (1, 2, 9000)),
+    ((6, 5000), (6, 1)),
+]
+
+
+@pytest.mark.parametrize("dtype,op", [("f32", "add"), ("i64", "add"), ("i32", "max"), ("bf16", "add"),
+                                      ("i64", "max")])
+@pytest.mark.parametrize("shape,k", LONG_ROWS, ids=[str(c[0]) + "k" + str(c[1]) for c in LONG_ROWS])
+def test_parity_long_rows(shape, k, dtype, op, monkeypatch):
+    # every shape the long-row pass can hold (by default only d = 2 rows of
+    # at most 4096 elements take it; the others take the dimension-1 schedule,
+    # which the rest of this file covers)
+    monkeypatch.setenv("EXSUM_LONGROW", "2")
+    seed = zlib.crc32(repr((shape, k, dtype, op, "long")).encode()) & 0xFFFFFF
+    dev, vals = seeded(shape, dtype, seed, op)
+    got = gpu_sum("excluded", to_device(dev, dtype), k, op)
+    check(got, oracle_sum("excluded", vals, k, op), dtype, op,
+          "long rows %s %s %s k=%s" % (dtype, op, shape, k))
