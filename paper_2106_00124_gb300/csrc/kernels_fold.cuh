@@ -210,9 +210,11 @@ k_plane_totals(const SP *__restrict__ P, int H, typename M::car_t *__restrict__ 
 // totals are scanned across the block (warp shuffles, then the warp totals),
 // in both directions.
 // ---------------------------------------------------------------------------
+// r_ready: R does not come from the kernel before (it is the input itself),
+// so the window of planes is read before waiting for that kernel (R2).
 template <class M, class SR = typename M::car_t, class ST = typename M::car_t>
 __device__ __forceinline__ void k_exc2d_body(const SR *__restrict__ R, const typename M::car_t *__restrict__ R2, ST *__restrict__ T, int n1,
-        int n2, int k1, int k2, int64_t vbid, int64_t vgrid)
+        int n2, int k1, int k2, int64_t vbid, int64_t vgrid, int r_ready = 0)
 {
     using A = typename M::acc_t;
     using C = typename M::car_t;
@@ -224,23 +226,7 @@ __device__ __forceinline__ void k_exc2d_body(const SR *__restrict__ R, const typ
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
     const int x1 = vbid;
     pdl_trigger();
-    pdl_wait();   // R and R2 come from the kernel before
-    // the one-dimensional part
-    A t2 = M::id();
-    for (int y0 = 0; y0 < n1; y0 += 4 * nt) {
-        C v[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int y = y0 + u * nt + tid;
-            v[u] = y < n1 ? R2[y] : M::template put<C>(M::id());
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int y = y0 + u * nt + tid;
-            if (y < n1 && (y < x1 || y >= x1 + k1)) t2 = M::op(t2, M::get(v[u]));
-        }
-    }
-    t2 = block_reduce<M>(t2, red);
+    if (!r_ready) pdl_wait();   // R and R2 come from the kernel before
     // window of k1 planes
     const int kw = min(k1, n1 - x1);
     for (int x2 = tid; x2 < n2; x2 += nt) {
@@ -258,6 +244,23 @@ __device__ __forceinline__ void k_exc2d_body(const SR *__restrict__ R, const typ
         }
         hv[x2] = h;
     }
+    if (r_ready) pdl_wait();   // R2 comes from the kernel before
+    // the one-dimensional part
+    A t2 = M::id();
+    for (int y0 = 0; y0 < n1; y0 += 4 * nt) {
+        C v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int y = y0 + u * nt + tid;
+            v[u] = y < n1 ? R2[y] : M::template put<C>(M::id());
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int y = y0 + u * nt + tid;
+            if (y < n1 && (y < x1 || y >= x1 + k1)) t2 = M::op(t2, M::get(v[u]));
+        }
+    }
+    t2 = block_reduce<M>(t2, red);
     __syncthreads();
     // scans along x2: thread segment [s0, s1)
     const int seg = (n2 + nt - 1) / nt;
@@ -421,9 +424,9 @@ __host__ __device__ inline int exc2d_w_warps(int n2, int acc)
 template <class M, class SR = typename M::car_t, class ST = typename M::car_t>
 __global__ void __launch_bounds__(256)
 k_exc2d(const SR *__restrict__ R, const typename M::car_t *__restrict__ R2, ST *__restrict__ T, int n1,
-        int n2, int k1, int k2)
+        int n2, int k1, int k2, int r_ready = 0)
 {
-    k_exc2d_body<M, SR, ST>(R, R2, T, n1, n2, k1, k2, blockIdx.x, gridDim.x);
+    k_exc2d_body<M, SR, ST>(R, R2, T, n1, n2, k1, k2, blockIdx.x, gridDim.x, r_ready);
 }
 
 }  // namespace exsum

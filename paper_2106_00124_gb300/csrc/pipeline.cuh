@@ -819,17 +819,18 @@ struct Pipe {
             k_plane_totals<MC, SP><<<(unsigned)n1, 256, 0, cx.stream>>>(P, H, Rw, R2, (int)n2);
         cx.check_launch();
         cx.before(TAG_EXC2D, n1 * n2);
-        exc2d_launch<CAR, CAR>(cx, R, R2, T, n1, n2, k1, k2, pdl);
+        exc2d_launch<CAR, CAR>(cx, R, R2, T, n1, n2, k1, k2, pdl, 0);
         cx.level--;
     }
 
     // Excluded sums of the n1 x n2 array R with box (k1, k2) from its plane
-    // totals R2: one warp per plane (k_exc2d_w) when there are planes enough
+    // totals R2 (r_ready: R is not written by the kernel before, so the block
+    // kernel reads its window of planes before waiting for R2): one warp per plane (k_exc2d_w) when there are planes enough
     // to fill the GPU that way, else one block per plane (k_exc2d: a few
     // planes each get a whole block's parallelism).
     template <class SR, class ST>
     static void exc2d_launch(Ctx &cx, const SR *R, const CAR *R2, ST *T, int64_t n1, int64_t n2, int64_t k1,
-                             int64_t k2, bool pdl)
+                             int64_t k2, bool pdl, int r_ready)
     {
         using Acc = typename MC::acc_t;
         if (n1 < 8 * cx.sms) {
@@ -838,9 +839,10 @@ struct Pipe {
             if (smem > 48 * 1024)
                 cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (pdl)
-                launch_pdl(kern, (unsigned)n1, 256, smem, cx.stream, R, R2, T, (int)n1, (int)n2, (int)k1, (int)k2);
+                launch_pdl(kern, (unsigned)n1, 256, smem, cx.stream, R, R2, T, (int)n1, (int)n2, (int)k1, (int)k2,
+                           r_ready);
             else
-                kern<<<(unsigned)n1, 256, smem, cx.stream>>>(R, R2, T, (int)n1, (int)n2, (int)k1, (int)k2);
+                kern<<<(unsigned)n1, 256, smem, cx.stream>>>(R, R2, T, (int)n1, (int)n2, (int)k1, (int)k2, r_ready);
             cx.check_launch();
             return;
         }
@@ -1013,7 +1015,7 @@ struct Pipe {
             k_plane_totals<MC, SIn><<<(unsigned)n[0], 256, 0, cx.stream>>>(X, 1, nullptr, R2, (int)n[1]);
             cx.check_launch();
             cx.before(TAG_EXC2D, N);
-            exc2d_launch<SIn, SOut>(cx, X, R2, out, n[0], n[1], k[0], k[1], true);
+            exc2d_launch<SIn, SOut>(cx, X, R2, out, n[0], n[1], k[0], k[1], true, 1);
             return;
         }
         RowPlan rp = row_plan(d, n, k, cx.sms);
