@@ -2,7 +2,7 @@
 // graph launch, with an autotuned schedule.
 //
 // Two schedules.  Levels (exsum_level.cu): the tensors the level kernels
-// take run as one persistent launch per pass level, the rest on one lane
+// take run as one launch per pass level (and register class), the rest on one lane
 // beside it.  Lanes: the tensors are assigned to `lanes` concurrent streams
 // (longest-processing-time first, or round-robin in size order), every lane
 // gets one workspace sized for its largest tensor (a lane runs its tensors

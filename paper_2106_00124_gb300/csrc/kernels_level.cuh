@@ -1,19 +1,19 @@
-// kernels_level.cuh -- persistent multi-tensor kernels: one launch runs one
-// pass level of the row schedule (Sec. 4) for every tensor of a batch.
+// kernels_level.cuh -- multi-tensor kernels: one launch runs one pass level
+// of the row schedule (Sec. 4) for every tensor of a batch.
 //
 // A batch of excluded sums is a set of independent pass chains (strided BDBS
 // pass, row totals, plane totals, the two-dimensional lower problem, the
 // final pass).  Instead of one launch per pass per tensor, the planner
-// (exsum_level.cu) writes, for each level, a work list of items: an item is
+// (exsum_level.cu) writes, for each level, a work list of items -- an item is
 // a run of consecutive virtual blocks of one pass of one tensor, with that
-// pass's parameters and the index of its first virtual block.  A level is
-// one launch of a persistent grid (a few blocks per SM) whose blocks pull
-// work-list slots from a device counter, one at a time, find the item that
-// holds the slot (the items are sorted by their first slot, and a block's
-// slots only increase) and run the pass body for that virtual block.  The
-// pass bodies are the single-tensor kernels' own (`*_body`), called with a
-// virtual block index and grid, so a tensor's results do not depend on
-// which physical block computed which part, nor on the order of the pulls.
+// pass's parameters and the index of its first virtual block -- and a table
+// giving the item of every work-list slot.  A level is one launch (per
+// register class): block b runs slot b, the hardware block scheduler handing
+// out the slots as blocks finish; or, as a tuning option, a persistent grid
+// of a few blocks per SM pulls slots from a device counter.  The pass bodies
+// are the single-tensor kernels' own (`*_body`), called with a virtual
+// block index and grid, so a tensor's results do not depend on which
+// physical block computed which part, nor on the order of the slots.
 #pragma once
 
 #include "kernels_fold.cuh"

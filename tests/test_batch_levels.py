@@ -1,5 +1,5 @@
-"""Level-scheduled batches: one persistent launch per pass level of the row
-schedule (Sec. 4) for every tensor of a batch, each launch pulling
+"""Level-scheduled batches: one launch per pass level (and register class)
+of the row schedule (Sec. 4) for every tensor of a batch, each launch taking
 (tensor, pass, tile) items from a device work list.
 
 GPU: every tensor of uneven batches is compared with the oracle, element by

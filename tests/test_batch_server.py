@@ -9,7 +9,7 @@ for fp32/bf16 +.  Beside that, each served result and each tensor of a
 batch planned on lanes gives the same bits as the same tensor computed alone
 by exsum_excluded (the kernels and their reduction order do not depend on
 what else runs), so that comparison is exact equality.  A level-scheduled
-batch (one persistent launch per pass level for all its tensors) may pick
+batch (one launch per pass level for all its tensors) may pick
 other tile heights than a lone call, so its tensors are held to the oracle
 bound only.
 """
