@@ -699,13 +699,15 @@ struct Pipe {
         }
     }
 
-    // Rows longer than one warp scans (k_rowx_long, one block of 512 threads
-    // per row, strips of V = 4 .. 32 elements): the row schedule without the
-    // window along n_{d-1} in the final pass.  The local suffixes of a row
-    // stay in shared memory: up to 16384 elements of 4 bytes, 8192 of 8.
-    // Taken by default for d = 2 and rows of at most 4096 elements, where it
-    // measured faster than the dimension-1 schedule; EXSUM_LONGROW=2 takes it
-    // for every shape it can hold, 0 never.
+    // Rows longer than one warp scans (k_rowx_long, one block per row,
+    // strips of 16 or 32 elements per thread -- long strips keep the block's
+    // compensated scans a small part of the work per element -- in blocks
+    // of 128 .. 512 threads): the row schedule without the window along
+    // n_{d-1} in the final pass.  The local suffixes of a row stay in shared
+    // memory: up to 16384 elements of 4 bytes, 8192 of 8.  Taken by default
+    // for d = 2 and rows of at most 4096 elements, where it measured faster
+    // than the dimension-1 schedule; EXSUM_LONGROW=2 takes it for every
+    // shape it can hold, 0 never.
     static constexpr int LONGROW_NT = 512;
     static RowPlan long_row_plan(int d, const int64_t *n)
     {
@@ -723,27 +725,28 @@ struct Pipe {
         return rp;
     }
 
-    template <class SF, class SOut, int V>
+    template <class SF, class SOut, int NT, int V>
     static void rowx_long_v(Ctx &cx, const SF *src, const CAR *T, SOut *out, int64_t rows, int64_t L, int k3)
     {
-        auto kern = k_rowx_long<M, SF, SOut, LONGROW_NT, V>;
-        const size_t smem = rowx_long_smem<M>(LONGROW_NT, V);
+        auto kern = k_rowx_long<M, SF, SOut, NT, V>;
+        const size_t smem = rowx_long_smem<M>(NT, V);
         if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        const int64_t grid = rows < cx.sms * 3 ? rows : cx.sms * 3;
-        kern<<<(unsigned)grid, LONGROW_NT, smem, cx.stream>>>(src, T, out, rows, (int)L, k3);
+        const int64_t cap = cx.sms * (2048 / NT);
+        const int64_t grid = rows < cap ? rows : cap;
+        kern<<<(unsigned)grid, NT, smem, cx.stream>>>(src, T, out, rows, (int)L, k3);
     }
 
     template <class SF, class SOut>
     static void rowx_long_go(Ctx &cx, const SF *src, const CAR *T, SOut *out, int64_t rows, int64_t L, int k3)
     {
-        if (L <= LONGROW_NT * 4)
-            rowx_long_v<SF, SOut, 4>(cx, src, T, out, rows, L, k3);
-        else if (L <= LONGROW_NT * 8)
-            rowx_long_v<SF, SOut, 8>(cx, src, T, out, rows, L, k3);
-        else if (L <= LONGROW_NT * 16)
-            rowx_long_v<SF, SOut, 16>(cx, src, T, out, rows, L, k3);
+        if (L <= 128 * 16)
+            rowx_long_v<SF, SOut, 128, 16>(cx, src, T, out, rows, L, k3);
+        else if (L <= 256 * 16)
+            rowx_long_v<SF, SOut, 256, 16>(cx, src, T, out, rows, L, k3);
+        else if (L <= 512 * 16)
+            rowx_long_v<SF, SOut, 512, 16>(cx, src, T, out, rows, L, k3);
         else if constexpr (sizeof(L_) == 4)
-            rowx_long_v<SF, SOut, 32>(cx, src, T, out, rows, L, k3);
+            rowx_long_v<SF, SOut, 512, 32>(cx, src, T, out, rows, L, k3);
     }
 
     template <class SF, class SOut>

@@ -91,6 +91,10 @@ WORKLOADS = {
     # 512^3 float32: larger than L2, for HBM-true per-pass figures
     "d3_512cube_f32_add_k8": dict(shape=(512, 512, 512), k=(8, 8, 8), dtype="f32", op="add",
                                   seed=10),
+    # boxes over 32 along the strided dimensions (suffixes kept in the output)
+    "d3_256cube_f32_add_k64": dict(shape=(256, 256, 256), k=(64, 64, 64), dtype="f32", op="add", seed=12),
+    # rows longer than one warp scans: the row schedule's one-block-per-row final pass
+    "d2_4096x2048_f32_add_k8": dict(shape=(4096, 2048), k=(8, 8), dtype="f32", op="add", seed=13),
     # rows whose length (301) is not a multiple of 4, larger than L2: the
     # realigned bulk final pass
     "d3_256x512x301_f32_add_k484": dict(shape=(256, 512, 301), k=(4, 8, 4), dtype="f32", op="add",
