@@ -456,9 +456,7 @@ def run_ours(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
             "data": "synthetic (seeded Philox, uniform; shapes of the paper's workloads)",
-            "config": {"workload": args.workload, "shape": list(shape), "k": list(k), "op": op,
-                       "l2": "flushed between steps (256 MiB write + read back, outside the timed spans)",
-                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "config": workload_config(args.workload, shape, k, op, world),
             "roofline": roofline,
             "one_read_one_write": {"bytes": one_rw, "achieved_gbs":
                                    round(one_rw / (ms_per_step * 1e-3) / 1e9, 1),
@@ -563,6 +561,15 @@ def cpu_all_cores(vals, spec, budget_s):
 
 # ---- reference arm: the CPU oracle -------------------------------------------------------------
 
+def workload_config(workload, shape, k, op, world):
+    """The `config` of a single-workload line: the workload, how the timed
+    steps treat the L2, and how ranks split the work.  Both arms print the
+    same object, so that their lines describe one configuration."""
+    return {"workload": workload, "shape": list(shape), "k": list(k), "op": op,
+            "l2": "flushed between steps (256 MiB write + read back, outside the timed spans)",
+            "parallelism": "replicas" if world > 1 else "single GPU"}
+
+
 def run_reference(args):
     import numpy as np
     from oracle import oracle
@@ -603,7 +610,7 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(dt * 1e3 / args.steps, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": spec["dtype"], "data": "synthetic",
-        "config": {"workload": args.workload, "shape": list(shape), "k": list(k), "op": op},
+        "config": workload_config(args.workload, shape, k, op, world),
         "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": desc},
         "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0,
